@@ -1,0 +1,395 @@
+"""Plain CPU oracle for the 3D multiscale DRT of planes and DJT of lines.
+
+TEST INFRASTRUCTURE ONLY.  This package is the independent reference that the
+GPU library is checked against.  Only ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` may import it.  It shares no code with
+the CUDA library (``paper_2501_13664_gb300``) and never imports it.
+
+The arithmetic lives in ``drt3d_oracle.c`` (plain C, compiled with gcc on first
+use); this module only marshals numpy arrays.  Paper references are to
+Marichal-Hernandez et al., "Three-dimensional multiscale discrete Radon and
+John transforms" (arXiv 2501.13664):
+
+* ``lline``                 -- eq.(digitalLine), Section 2.1
+* ``planes_brute``          -- eq.(3DfDRT), Section 3.1 (definition, scatter)
+* ``planes_alg1``           -- Algorithm 1 with eq.(map3D)
+* ``planes_forward``        -- Algorithm 2's twelve dodecants (input remap)
+* ``planes_adjoint``        -- Section 5.1, eq.(invmap3Dsummation)
+* ``planes_inverse``        -- exact integer stage inverse derived from
+                               eq.(map2D)/eq.(map3D) and Algorithm 1's zero
+                               embedding (the paper's own inverse is the
+                               iterative scheme of Section 5.2)
+* ``lines_brute``           -- eq.(3DfDJT), Section 4.1
+* ``lines_alg3``            -- Algorithm 3 with eq.(map3DJ)
+* ``lines_forward``         -- the twelve line sectors of Section 4.1
+
+Every function is pinned by ``tests/test_oracle_*.py`` against closed forms,
+invariants and brute force; ``cond_number`` (Table "condNumber") is the one
+quantity whose paper values are not reproduced ("parity unpinned").
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "drt3d_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle_drt3d.so")
+_lock = threading.Lock()
+_lib = None
+
+N_DODECANTS = 12
+N_SECTORS = 12
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc into ``oracle/_build`` and return its path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        I = ctypes.c_int
+        I64 = ctypes.c_int64
+        sig = {
+            "drto_lline": (I64, [I, I64, I64]),
+            "drto_dodecant_src": (I64, [I, I, I, I, I]),
+            "drto_sector_src": (I64, [I, I, I, I, I]),
+            "drto_gather_dodecant_4": (None, [I, I, P, P]),
+            "drto_gather_dodecant_8": (None, [I, I, P, P]),
+            "drto_scatter_add_dodecant_f64": (None, [I, I, P, P]),
+            "drto_scatter_add_dodecant_i32": (None, [I, I, P, P]),
+            "drto_gather_sector_4": (None, [I, I, P, P]),
+            "drto_dodecant_index_table": (None, [I, I, P]),
+            "drto_sector_index_table": (None, [I, I, P]),
+            "drto_planes_brute_i64": (None, [I, P, P]),
+            "drto_planes_brute_f64": (None, [I, P, P]),
+            "drto_planes_cell_i64": (I64, [I, P, I, I, I]),
+            "drto_planes_adjoint_brute_f64": (None, [I, P, P]),
+            "drto_planes_alg1_i32": (I, [I, P, P]),
+            "drto_planes_alg1_f64": (I, [I, P, P]),
+            "drto_planes_adjoint_i32": (I, [I, P, P]),
+            "drto_planes_adjoint_f64": (I, [I, P, P]),
+            "drto_planes_inverse_i32": (I, [I, P, P]),
+            "drto_lines_brute_i64": (None, [I, P, P]),
+            "drto_lines_cell_i64": (I64, [I, P, I, I, I, I]),
+            "drto_lines_alg3_i32": (I, [I, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check_N(N: int) -> int:
+    if N < 2 or N > 1024 or (N & (N - 1)):
+        raise ValueError(f"N must be a power of two in [2, 1024], got {N}")
+    return N.bit_length() - 1
+
+
+def _cube(f: np.ndarray) -> int:
+    if f.ndim != 3 or not (f.shape[0] == f.shape[1] == f.shape[2]):
+        raise ValueError(f"expected an N x N x N volume, got shape {f.shape}")
+    N = f.shape[0]
+    _check_N(N)
+    return N
+
+
+# --------------------------------------------------------------------------
+# Geometry
+# --------------------------------------------------------------------------
+def lline(n: int, s: int, u: int) -> int:
+    """l^n_s(u) of eq.(digitalLine)."""
+    return int(_load().drto_lline(n, s, u))
+
+
+def lline_table(N: int) -> np.ndarray:
+    """Table T[s][u] = l^n_s(u) for s, u in [0, N)."""
+    n = _check_N(N)
+    lib = _load()
+    return np.array([[lib.drto_lline(n, s, u) for u in range(N)] for s in range(N)], dtype=np.int64)
+
+
+def dodecant_src_index(N: int, k: int) -> np.ndarray:
+    """Flat index into f of g_k(x', y', z') for every (x', y', z'), shape N^3."""
+    idx = np.empty((N, N, N), dtype=np.int64)
+    _load().drto_dodecant_index_table(N, k, _ptr(idx))
+    return idx
+
+
+def sector_src_index(N: int, k: int) -> np.ndarray:
+    """Flat index into f of sector k's frame volume at every (x', y', z')."""
+    idx = np.empty((N, N, N), dtype=np.int64)
+    _load().drto_sector_index_table(N, k, _ptr(idx))
+    return idx
+
+
+def dodecant_volume(f: np.ndarray, k: int) -> np.ndarray:
+    """g_k = f seen in dodecant k's frame (Algorithm 2 input permute/flip)."""
+    N = _cube(f)
+    f = np.ascontiguousarray(f)
+    if f.dtype.itemsize == 4:
+        g = np.empty_like(f)
+        _load().drto_gather_dodecant_4(N, k, _ptr(f), _ptr(g))
+    elif f.dtype.itemsize == 8:
+        g = np.empty_like(f)
+        _load().drto_gather_dodecant_8(N, k, _ptr(f), _ptr(g))
+    else:
+        g = dodecant_volume(f.astype(np.int32), k).astype(f.dtype)
+    return g
+
+
+def sector_volume(f: np.ndarray, k: int) -> np.ndarray:
+    """f seen in DJT sector k's frame (x' along the driving axis)."""
+    N = _cube(f)
+    f = np.ascontiguousarray(f)
+    if f.dtype.itemsize != 4:
+        return sector_volume(f.astype(np.int32), k).astype(f.dtype)
+    g = np.empty_like(f)
+    _load().drto_gather_sector_4(N, k, _ptr(f), _ptr(g))
+    return g
+
+
+# --------------------------------------------------------------------------
+# Planes
+# --------------------------------------------------------------------------
+def planes_brute(g: np.ndarray) -> np.ndarray:
+    """eq.(3DfDRT) by scatter, one dodecant frame.  int64 or float64 output."""
+    N = _cube(g)
+    R = None
+    if np.issubdtype(g.dtype, np.floating):
+        gg = np.ascontiguousarray(g, dtype=np.float64)
+        R = np.empty((N, N, 3 * N), dtype=np.float64)
+        _load().drto_planes_brute_f64(N, _ptr(gg), _ptr(R))
+    else:
+        gg = np.ascontiguousarray(g, dtype=np.int64)
+        R = np.empty((N, N, 3 * N), dtype=np.int64)
+        _load().drto_planes_brute_i64(N, _ptr(gg), _ptr(R))
+    return R
+
+
+def planes_cell(g: np.ndarray, s1: int, s2: int, d: int) -> int:
+    """One output cell of eq.(3DfDRT), exact int64, one dodecant frame."""
+    N = _cube(g)
+    gg = np.ascontiguousarray(g, dtype=np.int32)
+    return int(_load().drto_planes_cell_i64(N, _ptr(gg), s1, s2, d))
+
+
+def planes_alg1(g: np.ndarray) -> np.ndarray:
+    """Algorithm 1 for one dodecant frame: int32 (wrapping) or float64."""
+    N = _cube(g)
+    lib = _load()
+    if np.issubdtype(g.dtype, np.floating):
+        gg = np.ascontiguousarray(g, dtype=np.float64)
+        R = np.empty((N, N, 3 * N), dtype=np.float64)
+        rc = lib.drto_planes_alg1_f64(N, _ptr(gg), _ptr(R))
+    else:
+        gg = np.ascontiguousarray(g.astype(np.int32, copy=False))
+        R = np.empty((N, N, 3 * N), dtype=np.int32)
+        rc = lib.drto_planes_alg1_i32(N, _ptr(gg), _ptr(R))
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    return R
+
+
+def planes_forward(f: np.ndarray, dodecants=range(N_DODECANTS), exact: str = "alg1") -> np.ndarray:
+    """All requested dodecants: out[i] is dodecant ``dodecants[i]``.
+
+    Integer inputs give int32 (wrapping) results, floating inputs float64.
+    ``exact='brute'`` uses the eq.(3DfDRT) scatter instead of Algorithm 1.
+    """
+    N = _cube(f)
+    ks = list(dodecants)
+    is_float = np.issubdtype(f.dtype, np.floating)
+    base = f.astype(np.float64) if is_float else f.astype(np.int32)
+    outs = []
+    for k in ks:
+        g = dodecant_volume(base, k)
+        if exact == "brute":
+            R = planes_brute(g)
+            outs.append(R if is_float else R.astype(np.int64).astype(np.int32, casting="unsafe"))
+        else:
+            outs.append(planes_alg1(g))
+    return np.stack(outs) if outs else np.empty((0, N, N, 3 * N))
+
+
+def planes_adjoint(Rbar: np.ndarray, dodecants=range(N_DODECANTS)) -> np.ndarray:
+    """Backprojection summed over dodecants: sum_k g_k^T(A_k^T Rbar[i]).
+
+    ``Rbar`` has shape (len(dodecants), N, N, 3N); int32 (wrapping) or float64.
+    Dodecants are accumulated in the given order.
+    """
+    ks = list(dodecants)
+    N = Rbar.shape[1]
+    _check_N(N)
+    lib = _load()
+    is_float = np.issubdtype(Rbar.dtype, np.floating)
+    if is_float:
+        acc = np.zeros((N, N, N), dtype=np.float64)
+        for i, k in enumerate(ks):
+            rb = np.ascontiguousarray(Rbar[i], dtype=np.float64)
+            gb = np.empty((N, N, N), dtype=np.float64)
+            if lib.drto_planes_adjoint_f64(N, _ptr(rb), _ptr(gb)) != 0:
+                raise MemoryError
+            lib.drto_scatter_add_dodecant_f64(N, k, _ptr(gb), _ptr(acc))
+    else:
+        acc = np.zeros((N, N, N), dtype=np.int32)
+        for i, k in enumerate(ks):
+            rb = np.ascontiguousarray(Rbar[i], dtype=np.int32)
+            gb = np.empty((N, N, N), dtype=np.int32)
+            if lib.drto_planes_adjoint_i32(N, _ptr(rb), _ptr(gb)) != 0:
+                raise MemoryError
+            lib.drto_scatter_add_dodecant_i32(N, k, _ptr(gb), _ptr(acc))
+    return acc
+
+
+def planes_adjoint_frame(Rbar_k: np.ndarray) -> np.ndarray:
+    """Adjoint of Algorithm 1 alone (one dodecant frame, no remap)."""
+    N = Rbar_k.shape[0]
+    lib = _load()
+    if np.issubdtype(Rbar_k.dtype, np.floating):
+        rb = np.ascontiguousarray(Rbar_k, dtype=np.float64)
+        gb = np.empty((N, N, N), dtype=np.float64)
+        rc = lib.drto_planes_adjoint_f64(N, _ptr(rb), _ptr(gb))
+    else:
+        rb = np.ascontiguousarray(Rbar_k, dtype=np.int32)
+        gb = np.empty((N, N, N), dtype=np.int32)
+        rc = lib.drto_planes_adjoint_i32(N, _ptr(rb), _ptr(gb))
+    if rc != 0:
+        raise MemoryError
+    return gb
+
+
+def planes_adjoint_brute_frame(Rbar_k: np.ndarray) -> np.ndarray:
+    """Transpose of the eq.(3DfDRT) scatter, one dodecant frame, float64."""
+    N = Rbar_k.shape[0]
+    rb = np.ascontiguousarray(Rbar_k, dtype=np.float64)
+    gb = np.empty((N, N, N), dtype=np.float64)
+    _load().drto_planes_adjoint_brute_f64(N, _ptr(rb), _ptr(gb))
+    return gb
+
+
+def planes_inverse(R_k: np.ndarray, k: int = 0):
+    """Exact integer inverse of dodecant k's transform.
+
+    Returns ``(f, in_range)``: the volume in the original frame (int32) and
+    whether ``R_k`` lies in the range of the forward map.
+    """
+    N = R_k.shape[0]
+    _check_N(N)
+    rr = np.ascontiguousarray(R_k, dtype=np.int32)
+    g = np.empty((N, N, N), dtype=np.int32)
+    rc = _load().drto_planes_inverse_i32(N, _ptr(rr), _ptr(g))
+    if rc < 0:
+        raise MemoryError
+    # back to the original frame: f[src(x',y',z')] = g[x',y',z']
+    f = np.empty(N * N * N, dtype=np.int32)
+    f[dodecant_src_index(N, k).ravel()] = g.ravel()
+    return f.reshape(N, N, N), rc == 0
+
+
+# --------------------------------------------------------------------------
+# Lines
+# --------------------------------------------------------------------------
+def lines_brute(g: np.ndarray) -> np.ndarray:
+    """eq.(3DfDJT) by scatter, one sector frame, int64, shape (N,N,2N,2N)."""
+    N = _cube(g)
+    gg = np.ascontiguousarray(g, dtype=np.int64)
+    J = np.empty((N, N, 2 * N, 2 * N), dtype=np.int64)
+    _load().drto_lines_brute_i64(N, _ptr(gg), _ptr(J))
+    return J
+
+
+def lines_cell(g: np.ndarray, s1: int, s2: int, d1: int, d2: int) -> int:
+    """One output cell of eq.(3DfDJT), exact int64, one sector frame."""
+    N = _cube(g)
+    gg = np.ascontiguousarray(g, dtype=np.int32)
+    return int(_load().drto_lines_cell_i64(N, _ptr(gg), s1, s2, d1, d2))
+
+
+def lines_alg3(g: np.ndarray) -> np.ndarray:
+    """Algorithm 3 for one sector frame, int32 wrapping, shape (N,N,2N,2N)."""
+    N = _cube(g)
+    gg = np.ascontiguousarray(g.astype(np.int32, copy=False))
+    J = np.empty((N, N, 2 * N, 2 * N), dtype=np.int32)
+    if _load().drto_lines_alg3_i32(N, _ptr(gg), _ptr(J)) != 0:
+        raise MemoryError("oracle allocation failed")
+    return J
+
+
+def lines_forward(f: np.ndarray, sectors=range(N_SECTORS), exact: str = "alg3") -> np.ndarray:
+    """Requested sectors of the DJT: out[i] is sector ``sectors[i]`` (int32)."""
+    _cube(f)
+    base = f.astype(np.int32)
+    outs = []
+    for k in sectors:
+        g = sector_volume(base, k)
+        if exact == "brute":
+            outs.append(lines_brute(g).astype(np.int32, casting="unsafe"))
+        else:
+            outs.append(lines_alg3(g))
+    return np.stack(outs)
+
+
+def lines_cell_global(f: np.ndarray, k: int, s1: int, s2: int, d1: int, d2: int) -> int:
+    """One DJT cell of sector k, computed from the original-frame volume."""
+    N = _cube(f)
+    lib = _load()
+    n = N.bit_length() - 1
+    acc = 0
+    ff = f.reshape(-1)
+    for x in range(N):
+        y = lib.drto_lline(n, s1, x) + d1 - N
+        z = lib.drto_lline(n, s2, x) + d2 - N
+        if 0 <= y < N and 0 <= z < N:
+            acc += int(ff[lib.drto_sector_src(N, k, x, y, z)])
+    return acc
+
+
+def planes_cell_global(f: np.ndarray, k: int, s1: int, s2: int, d: int) -> int:
+    """One planes cell of dodecant k, computed from the original-frame volume."""
+    N = _cube(f)
+    g = dodecant_volume(f.astype(np.int32), k)
+    return planes_cell(g, s1, s2, d)
+
+
+# --------------------------------------------------------------------------
+# Dense operator (tiny N) for condition numbers (Table "condNumber").
+# --------------------------------------------------------------------------
+def planes_matrix(N: int) -> np.ndarray:
+    """Dense matrix of the 12-dodecant forward operator, rows = output cells."""
+    cols = []
+    for i in range(N ** 3):
+        e = np.zeros(N ** 3, dtype=np.int32)
+        e[i] = 1
+        cols.append(planes_forward(e.reshape(N, N, N)).reshape(-1).astype(np.float64))
+    return np.stack(cols, axis=1)
+
+
+def cond_number(N: int) -> float:
+    """sigma_max / sigma_min of the 12-dodecant operator.  Parity unpinned:
+    the paper's printed values are not reproduced by this operator."""
+    s = np.linalg.svd(planes_matrix(N), compute_uv=False)
+    return float(s[0] / s[-1])
