@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the 3D DRT-of-planes hot path on GB300.
+
+Workload (one "step"): one N=256 uint8 volume -- 1 % sparse voxels at 1..255
+plus 8 embedded digital planes of 255 -- through the 12-dodecant forward
+transform (int32 output, 2.4 GB) followed by the exact inverse round trip from
+one dodecant.  ``value`` is whole-job volumes/s with the input resident in HBM;
+``e2e`` is the same through the public API with host buffers (H2D of the
+volume and D2H of the transform and the reconstructed volume inside the timed
+region).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank transforms its own volume (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "N=256 DRT-of-planes volumes/s and HBM GB/s vs peak; batched vs one-by-one"
+UNIT = "volumes/s"
+L2_BYTES = 129 * 1024 * 1024
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--N", type=int, default=256)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args(argv)
+
+
+# --------------------------------------------------------------------------
+# distributed helpers (host logic; covered by gloo tests on CPU)
+# --------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world: int, backend: str):
+    import torch.distributed as dist
+
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Maximum of a per-rank float over all ranks (identity at world 1)."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Units processed by all ranks divided by the slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
+# --------------------------------------------------------------------------
+# clocks
+# --------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", self.gpu], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": FALLBACK_HBM_GBS, "source": "fallback"}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+# --------------------------------------------------------------------------
+def oracle_volume_seconds(f_u8, n_fwd: int = 2):
+    """Time the oracle on a bounded sample and extrapolate one step.
+
+    Returns (seconds per step, sample description)."""
+    import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    R = None
+    for k in range(n_fwd):
+        R = oracle.planes_forward(f_u8, dodecants=[k])[0]
+    t_fwd = (time.perf_counter() - t0) / n_fwd
+    t0 = time.perf_counter()
+    oracle.planes_inverse(R, n_fwd - 1)
+    t_inv = time.perf_counter() - t0
+    sample = (f"oracle (plain C, 1 thread): Algorithm 1 on {n_fwd} of 12 dodecants of one N=256 volume "
+              f"({t_fwd:.2f} s each) + exact inverse of one dodecant ({t_inv:.2f} s); "
+              f"step time extrapolated as 12 forwards + 1 inverse")
+    return 12 * t_fwd + t_inv, sample
+
+
+# --------------------------------------------------------------------------
+# reference arm: the oracle as it stands, on the host cores
+# --------------------------------------------------------------------------
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+
+    import oracle
+    import synth
+
+    oracle.build()
+    f = synth.c2_volume(args.N)
+
+    def step(i):
+        k = i % 12
+        R = oracle.planes_forward(f, dodecants=[k])[0]
+        t1 = time.perf_counter()
+        oracle.planes_inverse(R, k)
+        return time.perf_counter() - t1
+
+    for i in range(args.warmup):
+        step(i)
+    fwd, inv = [], []
+    t_all = time.perf_counter()
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        ti = step(i)
+        fwd.append(time.perf_counter() - t0 - ti)
+        inv.append(ti)
+    wall = time.perf_counter() - t_all
+    t_vol = 12 * statistics.mean(fwd) + statistics.mean(inv)
+    value = 1.0 / t_vol
+    sample = ("per step: Algorithm 1 on one of the 12 dodecants (rotating) + exact inverse of it, plain C "
+              "oracle on 1 host thread; volume time = 12 x mean forward + mean inverse")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+        "config": {"workload": f"N={args.N} uint8 sparse volume + 8 planes: 12-dodecant forward + exact "
+                               "inverse round trip", "N": args.N},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist_init(world, "nccl")
+
+    import paper_2501_13664_gb300 as drt3d
+    import synth
+
+    N = args.N
+    f_np = synth.c2_volume(N, seed=2 + rank)
+    vol = torch.from_numpy(f_np).to(dev)
+    plan = drt3d.get_plan(N, torch.uint8)
+    out = torch.empty((12, N, N, 3 * N), dtype=torch.int32, device=dev)
+    ws = plan.workspace("planes_forward")
+    inv_k = 0
+    inv_out = torch.empty((N, N, N), dtype=torch.int32, device=dev)
+    have_inverse = hasattr(drt3d, "planes_inverse")
+    iplan = drt3d.get_plan(N, torch.int32) if have_inverse else None
+    iws = iplan.workspace("planes_inverse") if have_inverse else None
+
+    def step():
+        drt3d.planes_forward(vol, drt3d.ALL, out=out, workspace=ws)
+        if have_inverse:
+            drt3d.planes_inverse(out[inv_k], inv_k, out=inv_out, workspace=iws, check=False)
+
+    # correctness guard on this very launch configuration
+    step()
+    torch.cuda.synchronize()
+    if have_inverse:
+        assert torch.equal(inv_out, vol.to(torch.int32)), "round trip failed"
+        assert iplan.device_error() == 0
+
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    plan.set_profiling(True)
+    if have_inverse:
+        iplan.set_profiling(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] \
+        if os.environ.get("CUDA_VISIBLE_DEVICES") else str(local)
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(i)  # evict L2 between timed steps (untimed)
+        starts[i].record()
+        step()
+        ends[i].record()
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_local = sum(step_ms) / len(step_ms)
+    ms = max_over_ranks(ms_local, world, dev)
+    value = whole_job_rate(1.0, world, ms / 1000.0)
+
+    launches = plan.profiled_launches() + (iplan.profiled_launches() if have_inverse else [])
+    plan.set_profiling(False)
+    if have_inverse:
+        iplan.set_profiling(False)
+    by_name: dict = {}
+    for name, t, b in launches:
+        e = by_name.setdefault(name, [0.0, 0, 0.0])
+        e[0] += t
+        e[1] += 1
+        e[2] = b
+    dom = max(by_name.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_tot, dom_cnt, dom_bytes) = dom
+    dom_ms = dom_tot / dom_cnt
+    peaks = measured_peaks()
+    achieved = dom_bytes / (dom_ms / 1000.0) / 1e9
+    floor_bytes = 12.0 * N * N * (3 * N - 2) * 4 + N ** 3  # input once + final output
+    kernels = {nm: {"launches": c, "avg_ms": tot / c, "algo_bytes": b,
+                    "gbs": b / (tot / c / 1000.0) / 1e9} for nm, (tot, c, b) in by_name.items()}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+        "config": {
+            "workload": f"N={N} uint8 volume (1% voxels 1..255 + 8 digital planes of 255): 12-dodecant "
+                        "forward (int32) + exact inverse round trip from one dodecant",
+            "N": N, "dodecants": 12, "input_dtype": "u8",
+            "l2": "flushed between timed steps by writing a 258 MB buffer (untimed)",
+            "inverse_in_step": have_inverse,
+        },
+        "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "peak_source": peaks["source"], "avg_ms": dom_ms, "algo_bytes_per_launch": dom_bytes},
+        "hbm_floor_gbs": floor_bytes / (ms / 1000.0) / 1e9,
+        "kernels": kernels,
+        "gpu_launches": len(launches),
+        "clocks": clk,
+    }
+
+    if not args.no_e2e:
+        pin_in = torch.from_numpy(f_np).pin_memory()
+        pin_out = torch.empty((12, N, N, 3 * N), dtype=torch.int32).pin_memory()
+        pin_inv = torch.empty((N, N, N), dtype=torch.int32).pin_memory()
+        vol_d = torch.empty_like(vol)
+        e2e_t = []
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            vol_d.copy_(pin_in, non_blocking=True)
+            drt3d.planes_forward(vol_d, drt3d.ALL, out=out, workspace=ws)
+            if have_inverse:
+                drt3d.planes_inverse(out[inv_k], inv_k, out=inv_out, workspace=iws, check=False)
+            pin_out.copy_(out, non_blocking=True)
+            if have_inverse:
+                pin_inv.copy_(inv_out, non_blocking=True)
+            torch.cuda.synchronize()
+            if i > 0:
+                e2e_t.append(time.perf_counter() - t0)
+        e2e_s = max_over_ranks(statistics.mean(e2e_t), world, dev)
+        line["e2e"] = {"value": whole_job_rate(1.0, world, e2e_s), "unit": UNIT,
+                       "h2d_bytes_per_step": int(pin_in.numel()),
+                       "d2h_bytes_per_step": int(pin_out.numel() * 4 + (pin_inv.numel() * 4 if have_inverse else 0))}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_cpu, sample = oracle_volume_seconds(f_np)
+        line["cpu_baseline"] = {"value": 1.0 / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": sample}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

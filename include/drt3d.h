@@ -1,0 +1,193 @@
+/*
+ * drt3d.h -- C ABI of libdrt3d, a GB300 (sm_103a) library for the 3D
+ * multiscale discrete Radon transform (DRT) of planes and discrete John
+ * transform (DJT) of lines of Marichal-Hernandez et al., "Three-dimensional
+ * multiscale discrete Radon and John transforms" (arXiv 2501.13664).
+ *
+ * General conventions
+ * -------------------
+ *  - Every function returns a drt3d_status and never throws.  Argument errors
+ *    are detected and returned synchronously, before anything is enqueued.
+ *  - All compute is enqueued asynchronously on the caller's CUDA stream
+ *    (0 = legacy default stream).  Errors raised inside a kernel (for example
+ *    an inverse input that is not in the range of the forward map) are
+ *    recorded in a device status word and read back by
+ *    drt3d_get_device_error().
+ *  - The caller owns every device buffer (inputs, outputs, workspaces).  The
+ *    library allocates no device memory on any compute call; a plan owns only
+ *    host metadata and one small device status word allocated at creation.
+ *  - Device pointers must be 16-byte aligned.
+ *  - N = 2^n with 2 <= N <= 1024 (Algorithms 1 and 3 take log2 N stages;
+ *    non-cubic sizes are left as future work in the paper's conclusions).
+ *  - Integer arithmetic is two's-complement int32 and wraps modulo 2^32, so
+ *    results are defined bit for bit for any input.
+ *
+ * Memory layouts (all C-contiguous)
+ * ---------------------------------
+ *  - Input volume f[x][y][z], N^3 elements of the plan's dtype.
+ *  - Planes output, one block per selected dodecant, in increasing dodecant
+ *    order: R[k][s1][s2][d], s1, s2 in [0, N), d in [0, 3N).  In dodecant k's
+ *    frame the cell sums the digital plane z' = l_{s1}(x') + l_{s2}(y') +
+ *    d - 2N (eq.(3DfDRT) with Algorithm 1's storage index, Section 3.1);
+ *    d = 0 and d = 1 are always zero.  Dodecant k's frame is
+ *    g_k(x', y', z') = f(...) given by Algorithm 2's InOrder table read as
+ *    "flip original axis j where entry j < 0, then new axis i takes original
+ *    axis |entry i|", with the rows of dodecants 5, 6, 9 and 10 taken as
+ *    [-3,1,2], [3,-1,2], [2,-3,1] and [-2,3,1] (the printed rows repeat two
+ *    sectors and miss two).
+ *  - Lines output, one block per selected sector, in increasing sector
+ *    order: J[k][s1][s2][d1][d2], d1, d2 in [0, 2N).  The cell sums the
+ *    digital line y' = l_{s1}(x') + d1 - N, z' = l_{s2}(x') + d2 - N
+ *    (eq.(3DfDJT), Algorithm 3's storage index, Section 4.1).  Sector
+ *    k = 4a + b drives along axis a (x, y, z); the two other axes follow in
+ *    cyclic order and bit 0 / bit 1 of b reverse the first / second of them.
+ *
+ * Digital line (eq.(digitalLine), Section 2.1):
+ *   l^n_s(u) = sum_{i=0}^{n-1} u_{n-1-i} * floor((floor(s / 2^i) + 1) / 2).
+ */
+#ifndef DRT3D_H
+#define DRT3D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum drt3d_status {
+    DRT3D_OK = 0,
+    DRT3D_ERR_INVALID_ARG = 1,  /* null plan/pointer, bad mask or dodecant index */
+    DRT3D_ERR_SIZE = 2,         /* N not a power of two, N < 2 or N > 1024 */
+    DRT3D_ERR_DTYPE = 3,        /* dtype not supported by this operation */
+    DRT3D_ERR_ALIGN = 4,        /* a device pointer is not 16-byte aligned */
+    DRT3D_ERR_WORKSPACE = 5,    /* workspace null or smaller than required */
+    DRT3D_ERR_NOT_IN_RANGE = 6, /* inverse input is not a forward transform */
+    DRT3D_ERR_TIMEOUT = 7,      /* a bounded device-side wait gave up */
+    DRT3D_ERR_BOUNDS = 8,       /* a device-side bounds check failed */
+    DRT3D_ERR_CUDA = 9,         /* a CUDA runtime call failed */
+    DRT3D_ERR_NO_MEMORY = 10    /* host allocation or plan status word failed */
+} drt3d_status;
+
+typedef enum drt3d_dtype {
+    DRT3D_U8 = 0,
+    DRT3D_I16 = 1,
+    DRT3D_I32 = 2,
+    DRT3D_F32 = 3
+} drt3d_dtype;
+
+/* Operation codes for drt3d_workspace_bytes(). */
+typedef enum drt3d_op {
+    DRT3D_OP_PLANES_FORWARD = 0,
+    DRT3D_OP_PLANES_ADJOINT = 1,
+    DRT3D_OP_PLANES_INVERSE = 2,
+    DRT3D_OP_LINES_FORWARD = 3
+} drt3d_op;
+
+#define DRT3D_ALL_DODECANTS 0xFFFu
+#define DRT3D_ALL_SECTORS 0xFFFu
+
+typedef struct drt3d_plan drt3d_plan;
+
+/* Create a plan for N^3 volumes of dtype `in_dtype`.  Planes forward accepts
+ * U8/I16/I32 (int32 output) and F32 (float output); the adjoint takes I32 or
+ * F32 plans; the inverse and the lines forward are integer only.  `flags` is
+ * reserved and must be 0.  On success *plan owns a 4-byte device status word
+ * on the current device.  Errors: INVALID_ARG (plan null, flags != 0), SIZE,
+ * DTYPE, NO_MEMORY, CUDA. */
+drt3d_status drt3d_plan_create(drt3d_plan** plan, int N, drt3d_dtype in_dtype, unsigned flags);
+
+/* Release a plan (NULL is accepted).  Waits for nothing: the caller must not
+ * destroy a plan while work that uses it is still in flight. */
+drt3d_status drt3d_plan_destroy(drt3d_plan* plan);
+
+/* Shape of the full 12-dodecant planes output: {12, N, N, 3N}. */
+drt3d_status drt3d_planes_out_shape(const drt3d_plan* plan, int64_t dims[4]);
+
+/* Shape of the full 12-sector lines output: {12, N, N, 2N, 2N}. */
+drt3d_status drt3d_lines_out_shape(const drt3d_plan* plan, int64_t dims[5]);
+
+/* Bytes of device workspace an operation needs for all 12 dodecants or
+ * sectors (a smaller mask never needs more).  `op` is a drt3d_op. */
+drt3d_status drt3d_workspace_bytes(const drt3d_plan* plan, int op, size_t* bytes);
+
+/* Forward 3D DRT of planes (Algorithm 1 per dodecant, Algorithm 2's twelve
+ * dodecants; stage map eq.(map3D), Section 3.1).
+ *   d_in   : N^3 volume of the plan's dtype, f[x][y][z].
+ *   d_out  : popcount(dodecant_mask) blocks of N*N*3N int32 (integer plans)
+ *            or float (F32 plans), R[k][s1][s2][d], overwritten.
+ *   dodecant_mask : bit k selects dodecant k (1..0xFFF).
+ *   d_ws, ws_bytes: workspace, >= drt3d_workspace_bytes(PLANES_FORWARD).
+ * Integer results are exact (wrapping int32); F32 results are rounded sums.
+ * Errors: INVALID_ARG, ALIGN, WORKSPACE, CUDA. */
+drt3d_status drt3d_planes_forward(const drt3d_plan* plan, const void* d_in, void* d_out,
+                                  uint32_t dodecant_mask, void* d_ws, size_t ws_bytes,
+                                  cudaStream_t stream);
+
+/* Adjoint (backprojection) of drt3d_planes_forward (Section 5.1, stage loop
+ * reversed with eq.(invmap3Dsummation); reads below d = 0 are zero):
+ *   d_vol = sum over selected k, in increasing k, of g_k^T(A_k^T d_cot[k]).
+ *   d_cot : popcount(mask) blocks of N*N*3N (int32 or float per the plan).
+ *   d_vol : N^3 int32 or float, overwritten.
+ * Plan dtype must be I32 or F32.  The dodecant sum has a fixed order, so F32
+ * results are deterministic.  Errors: INVALID_ARG, DTYPE, ALIGN, WORKSPACE,
+ * CUDA. */
+drt3d_status drt3d_planes_adjoint(const drt3d_plan* plan, const void* d_cot, void* d_vol,
+                                  uint32_t dodecant_mask, void* d_ws, size_t ws_bytes,
+                                  cudaStream_t stream);
+
+/* Exact inverse of one dodecant's planes transform (not printed in the
+ * paper: derived from eq.(map2D)/eq.(map3D) and Algorithm 1's zero embedding;
+ * the paper's own inverse is the iterative scheme of Section 5.2).  Each
+ * half-stage is undone by a suffix sum of out1 - out0 along d.
+ *   d_R   : N*N*3N int32, dodecant `dodecant`'s block of the forward output.
+ *   d_vol : N^3 int32 volume f[x][y][z] (original frame), overwritten.
+ * If d_R is not in the range of the forward map the volume is undefined and
+ * DRT3D_ERR_NOT_IN_RANGE is recorded in the device status word (read it with
+ * drt3d_get_device_error).  Integer plans only.  Errors: INVALID_ARG, DTYPE,
+ * ALIGN, WORKSPACE, CUDA. */
+drt3d_status drt3d_planes_inverse(const drt3d_plan* plan, const int32_t* d_R, int dodecant,
+                                  int32_t* d_vol, void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Forward 3D DJT of lines (Algorithm 3 per sector; stage map eq.(map3DJ),
+ * Section 4.1).
+ *   d_in  : N^3 volume of the plan's dtype (U8, I16 or I32).
+ *   d_out : popcount(sector_mask) blocks of N*N*2N*2N int32, overwritten.
+ * Errors: INVALID_ARG, DTYPE, ALIGN, WORKSPACE, CUDA. */
+drt3d_status djt3d_lines_forward(const drt3d_plan* plan, const void* d_in, int32_t* d_out,
+                                 uint32_t sector_mask, void* d_ws, size_t ws_bytes,
+                                 cudaStream_t stream);
+
+/* Synchronise `stream`, read and clear the plan's device status word.
+ * Returns DRT3D_OK if no kernel recorded an error since the last call. */
+drt3d_status drt3d_get_device_error(const drt3d_plan* plan, cudaStream_t stream);
+
+/* Human-readable name of a status code (static storage). */
+const char* drt3d_status_string(drt3d_status status);
+
+/* Diagnostics.  While profiling is enabled, every compute call made with the
+ * plan records a CUDA event pair around each of its kernel launches on the
+ * caller's stream (up to 2048 launches after enabling), with a short name and
+ * the launch's algorithmic bytes (compact rows read plus rows written: the
+ * HBM floor of that launch).  drt3d_set_profiling(plan, 1) clears the record;
+ * enabling creates events (no device memory).  Profiling state lives in the
+ * plan and is not thread-safe.
+ * drt3d_profiled_launches(): synchronises on the last recorded event, fills
+ * up to `capacity` entries of ms[] and algo_bytes[] (either may be NULL) and
+ * sets *count to the number of recorded launches. */
+drt3d_status drt3d_set_profiling(drt3d_plan* plan, int enable);
+drt3d_status drt3d_profiled_launches(const drt3d_plan* plan, float* ms, double* algo_bytes, int capacity,
+                                     int* count);
+/* Name of recorded launch i ("" if out of range). */
+const char* drt3d_profiled_launch_name(const drt3d_plan* plan, int i);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int drt3d_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DRT3D_H */

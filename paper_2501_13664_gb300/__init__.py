@@ -1,0 +1,194 @@
+"""GB300-native 3D multiscale discrete Radon transform of planes and discrete
+John transform of lines (Marichal-Hernandez et al., arXiv 2501.13664).
+
+This is the thin PyTorch-facing layer over the C-ABI library ``libdrt3d``
+(``include/drt3d.h``).  PyTorch provides device memory and streams; every
+arithmetic step runs in the library's sm_103a kernels.  There is no CPU
+fallback: if the library cannot be built or loaded, these functions raise.
+
+Public functions (device tensors in, device tensors out; a CPU input tensor is
+copied to the current CUDA device and the result copied back):
+
+* ``planes_forward(vol, dodecants)``   -> (k, N, N, 3N) int32 / float32
+* ``planes_adjoint(cot, dodecants)``   -> (N, N, N)
+* ``planes_inverse(R_k, dodecant)``    -> (N, N, N) int32
+* ``lines_forward(vol, sectors)``      -> (k, N, N, 2N, 2N) int32
+* ``PlanesTransform``                  -- torch.autograd.Function (float32)
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _abi
+from ._abi import DRT3DError
+
+ALL = 0xFFF
+
+_TORCH_DTYPES = {torch.uint8: "u8", torch.int16: "i16", torch.int32: "i32", torch.float32: "f32"}
+
+
+def _mask(sel) -> int:
+    if isinstance(sel, int):
+        m = sel
+    else:
+        m = 0
+        for k in sel:
+            if not 0 <= int(k) < 12:
+                raise ValueError(f"dodecant/sector index out of range: {k}")
+            m |= 1 << int(k)
+    if m <= 0 or m > ALL:
+        raise ValueError(f"bad dodecant/sector mask {m:#x}")
+    return m
+
+
+def _count(m: int) -> int:
+    return bin(m).count("1")
+
+
+class Plan:
+    """A libdrt3d plan for N^3 volumes of one dtype on the current device."""
+
+    def __init__(self, N: int, dtype: torch.dtype):
+        if dtype not in _TORCH_DTYPES:
+            raise TypeError(f"unsupported dtype {dtype}")
+        self.N = int(N)
+        self.dtype = dtype
+        self._lib = _abi.lib()
+        h = ctypes.c_void_p()
+        _abi.check(self._lib.drt3d_plan_create(ctypes.byref(h), self.N, _abi.DTYPES[_TORCH_DTYPES[dtype]], 0),
+                   "drt3d_plan_create")
+        self.handle = h
+        self.device = torch.cuda.current_device()
+
+    def workspace_bytes(self, op: str) -> int:
+        v = ctypes.c_size_t()
+        _abi.check(self._lib.drt3d_workspace_bytes(self.handle, _abi.OPS[op], ctypes.byref(v)),
+                   "drt3d_workspace_bytes")
+        return int(v.value)
+
+    def workspace(self, op: str) -> torch.Tensor:
+        return torch.empty(max(16, self.workspace_bytes(op)), dtype=torch.uint8, device=f"cuda:{self.device}")
+
+    def device_error(self, stream=None) -> int:
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        return int(self._lib.drt3d_get_device_error(self.handle, ctypes.c_void_p(s)))
+
+    def set_profiling(self, on: bool) -> None:
+        """Record per-launch CUDA-event times of this plan's calls (diagnostic)."""
+        _abi.check(self._lib.drt3d_set_profiling(self.handle, 1 if on else 0), "drt3d_set_profiling")
+
+    def profiled_launches(self) -> list:
+        """[(name, ms, algorithmic_bytes)] of every launch recorded since enabling."""
+        cnt = ctypes.c_int()
+        _abi.check(self._lib.drt3d_profiled_launches(self.handle, None, None, 0, ctypes.byref(cnt)),
+                   "drt3d_profiled_launches")
+        n = cnt.value
+        ms = (ctypes.c_float * max(1, n))()
+        by = (ctypes.c_double * max(1, n))()
+        _abi.check(self._lib.drt3d_profiled_launches(self.handle, ms, by, n, ctypes.byref(cnt)),
+                   "drt3d_profiled_launches")
+        return [(self._lib.drt3d_profiled_launch_name(self.handle, i).decode(), float(ms[i]), float(by[i]))
+                for i in range(n)]
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None):
+                self._lib.drt3d_plan_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+_plan_cache: dict = {}
+
+
+def get_plan(N: int, dtype: torch.dtype) -> Plan:
+    key = (torch.cuda.current_device(), int(N), dtype)
+    p = _plan_cache.get(key)
+    if p is None:
+        p = Plan(N, dtype)
+        _plan_cache[key] = p
+    return p
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _vol_check(vol: torch.Tensor) -> int:
+    if vol.dim() != 3 or not (vol.shape[0] == vol.shape[1] == vol.shape[2]):
+        raise ValueError(f"expected an N x N x N volume, got {tuple(vol.shape)}")
+    return int(vol.shape[0])
+
+
+def _to_device(t: torch.Tensor):
+    """(device tensor, came_from_host)."""
+    if t.is_cuda:
+        return t.contiguous(), False
+    return t.contiguous().pin_memory().to("cuda", non_blocking=True), True
+
+
+def planes_forward(vol: torch.Tensor, dodecants=ALL, out: torch.Tensor | None = None,
+                   workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """Forward 3D DRT of planes over the selected dodecants (Algorithms 1-2)."""
+    vol_d, host = _to_device(vol)
+    N = _vol_check(vol_d)
+    m = _mask(dodecants)
+    plan = get_plan(N, vol_d.dtype)
+    odt = torch.float32 if vol_d.dtype == torch.float32 else torch.int32
+    if out is None:
+        out = torch.empty((_count(m), N, N, 3 * N), dtype=odt, device=vol_d.device)
+    ws = workspace if workspace is not None else plan.workspace("planes_forward")
+    _abi.check(plan._lib.drt3d_planes_forward(plan.handle, vol_d.data_ptr(), out.data_ptr(), m,
+                                              ws.data_ptr(), ws.numel(), _stream()),
+               "drt3d_planes_forward")
+    if host:
+        return out.to("cpu")
+    return out
+
+
+def planes_adjoint(cot: torch.Tensor, dodecants=ALL, out: torch.Tensor | None = None,
+                   workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """Backprojection (Section 5.1), summed over the selected dodecants."""
+    cot_d, host = _to_device(cot)
+    m = _mask(dodecants)
+    if cot_d.dim() != 4 or cot_d.shape[0] != _count(m) or cot_d.shape[3] != 3 * cot_d.shape[1]:
+        raise ValueError(f"cotangent shape {tuple(cot_d.shape)} does not match the mask")
+    N = int(cot_d.shape[1])
+    plan = get_plan(N, cot_d.dtype)
+    if out is None:
+        out = torch.empty((N, N, N), dtype=cot_d.dtype, device=cot_d.device)
+    ws = workspace if workspace is not None else plan.workspace("planes_adjoint")
+    _abi.check(plan._lib.drt3d_planes_adjoint(plan.handle, cot_d.data_ptr(), out.data_ptr(), m,
+                                              ws.data_ptr(), ws.numel(), _stream()),
+               "drt3d_planes_adjoint")
+    return out.to("cpu") if host else out
+
+
+class PlanesTransform(torch.autograd.Function):
+    """Differentiable 3D DRT of planes for float32 volumes.
+
+    The operator is linear, so backward is the hand-written adjoint kernel
+    applied to the cotangent; nothing from the forward is saved.
+    """
+
+    @staticmethod
+    def forward(ctx, vol: torch.Tensor, dodecants: int = ALL):
+        if vol.dtype != torch.float32:
+            raise TypeError("PlanesTransform needs float32 volumes")
+        ctx.mask = _mask(dodecants)
+        return planes_forward(vol, ctx.mask)
+
+    @staticmethod
+    def backward(ctx, grad_out: torch.Tensor):
+        return planes_adjoint(grad_out.contiguous(), ctx.mask), None
+
+
+def planes(vol: torch.Tensor, dodecants=ALL) -> torch.Tensor:
+    """Autograd-aware forward for float32 volumes (batched over a leading dim)."""
+    m = _mask(dodecants)
+    if vol.dim() == 4:
+        return torch.stack([PlanesTransform.apply(v, m) for v in vol])
+    return PlanesTransform.apply(vol, m)

@@ -1,0 +1,410 @@
+// api.cu -- the extern "C" boundary of libdrt3d: plans, argument checks,
+// workspace carving and the pass schedules of the planes transforms.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+namespace drt3d {
+
+// Algorithm 2's InOrder table with the reading documented in drt3d.h: new
+// axis i of dodecant k is original axis |e_i| - 1, and original axis a is
+// reversed when its own entry e_a is negative.  Rows 5, 6, 9, 10 carry the
+// single-sign corrections that make the twelve sectors distinct.
+static const int kInOrder[12][3] = {
+    {1, 2, 3},   {-2, 1, 3},  {-1, -2, 3}, {2, -1, 3},   {-1, -3, -2}, {-3, 1, 2},
+    {3, -1, 2},  {1, 3, -2},  {-3, -2, -1}, {2, -3, 1},  {-2, 3, 1},   {3, 2, -1},
+};
+
+Affine dodecant_affine(int N, int k) {
+    const long long stride[3] = {(long long)N * N, (long long)N, 1};
+    long long s[3];
+    Affine A{0, 0, 0, 0};
+    for (int i = 0; i < 3; ++i) {
+        const int a = std::abs(kInOrder[k][i]) - 1;
+        if (kInOrder[k][a] < 0) {
+            A.o0 += (long long)(N - 1) * stride[a];
+            s[i] = -stride[a];
+        } else {
+            s[i] = stride[a];
+        }
+    }
+    A.sx = s[0];
+    A.sy = s[1];
+    A.sz = s[2];
+    return A;
+}
+
+Affine sector_affine(int N, int k) {
+    const long long stride[3] = {(long long)N * N, (long long)N, 1};
+    const int a = k >> 2, flips = k & 3;
+    Affine A{0, stride[a], 0, 0};
+    const int b = (a + 1) % 3, c = (a + 2) % 3;
+    if (flips & 1) { A.o0 += (long long)(N - 1) * stride[b]; A.sy = -stride[b]; }
+    else A.sy = stride[b];
+    if (flips & 2) { A.o0 += (long long)(N - 1) * stride[c]; A.sz = -stride[c]; }
+    else A.sz = stride[c];
+    return A;
+}
+
+static Geo planes_geo(int N, int mx, int my) {
+    const int lo = 2 * N + 2 - (1 << mx) - (1 << my);
+    Geo g;
+    g.base = lo & ~7;
+    g.pitch = (int)align_up((size_t)(3 * N - g.base), 8);
+    return g;
+}
+
+PlanesSchedule make_planes_schedule(int N) {
+    PlanesSchedule S{};
+    const int n = ilog2(N);
+    const int ngroups = (n + 3) / 4;
+    int sizes[8];
+    for (int g = 0; g < ngroups; ++g) sizes[g] = n / ngroups + (g < n % ngroups ? 1 : 0);
+    int mx = 0, my = 0, p = 0;
+    size_t maxel = 0;
+    Geo prev{0, 0};
+    for (int g = 0; g < ngroups; ++g) {
+        for (int axis = 0; axis < 2; ++axis) {
+            PassSpec& P = S.pass[p];
+            P.axis = axis;
+            P.G = sizes[g];
+            P.m0 = axis == 0 ? mx : my;
+            P.in = prev;
+            P.ingest = (p == 0);
+            if (axis == 0) mx += P.G; else my += P.G;
+            P.final_ = (g == ngroups - 1 && axis == 1);
+            P.out = P.final_ ? Geo{0, 3 * N} : planes_geo(N, mx, my);
+            if (!P.final_) {
+                const size_t el = (size_t)N * N * P.out.pitch;
+                if (el > maxel) maxel = el;
+            }
+            prev = P.out;
+            ++p;
+        }
+    }
+    S.npass = p;
+    S.buf_elems = maxel;
+    return S;
+}
+
+static size_t planes_buf_bytes(const drt3d_plan* P) {
+    return align_up(P->planes.buf_elems * 4, 256);
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+static int popcount12(uint32_t m) {
+    int c = 0;
+    for (int k = 0; k < 12; ++k) c += (m >> k) & 1;
+    return c;
+}
+
+constexpr int kLanesK = 4;  // displacements per lane in planes_pass.cu
+
+static int warp_tile_valid(int G) { return (32 * kLanesK - ((1 << G) - 1)) & ~3; }
+
+// Profiling helpers: no-ops unless drt3d_set_profiling(plan, 1).
+static void prof_begin(const drt3d_plan* P, cudaStream_t s, const char* name, double bytes) {
+    Profiler& pr = P->prof;
+    if (!pr.on || pr.count >= kMaxLaunch) return;
+    cudaEventRecord(pr.ev[2 * pr.count], s);
+    pr.bytes[pr.count] = bytes;
+    std::snprintf(pr.name[pr.count], sizeof(pr.name[0]), "%s", name);
+}
+static void prof_end(const drt3d_plan* P, cudaStream_t s) {
+    Profiler& pr = P->prof;
+    if (!pr.on || pr.count >= kMaxLaunch) return;
+    cudaEventRecord(pr.ev[2 * pr.count + 1], s);
+    ++pr.count;
+}
+
+// Algorithmic bytes of one planes pass for one dodecant: the compact rows it
+// must read (d >= lo of its input stage, or the volume) plus the rows it
+// writes (d >= lo of its output stage, or the full public 3N rows).
+static double planes_pass_bytes(const drt3d_plan* P, const PassSpec& ps, int mx0, int my0, bool adjoint) {
+    const double N = P->N;
+    const int mx1 = mx0 + (ps.axis == 0 ? ps.G : 0), my1 = my0 + (ps.axis == 1 ? ps.G : 0);
+    const double lo_in = 2 * N + 2 - (1 << mx0) - (1 << my0);
+    const double lo_out = 2 * N + 2 - (1 << mx1) - (1 << my1);
+    const double item = adjoint ? 4.0 : (P->dtype == DRT3D_U8 ? 1.0 : P->dtype == DRT3D_I16 ? 2.0 : 4.0);
+    const double vol = N * N * N * (ps.ingest ? item : 4.0);
+    const double in_b = ps.ingest ? vol : N * N * (3 * N - lo_in) * 4.0;
+    const double out_b = ps.final_ ? N * N * 3 * N * 4.0 : N * N * (3 * N - lo_out) * 4.0;
+    return in_b + out_b;
+}
+
+}  // namespace drt3d
+
+using namespace drt3d;
+
+extern "C" {
+
+int drt3d_version(void) { return 100; }
+
+const char* drt3d_status_string(drt3d_status s) {
+    switch (s) {
+    case DRT3D_OK: return "DRT3D_OK";
+    case DRT3D_ERR_INVALID_ARG: return "DRT3D_ERR_INVALID_ARG";
+    case DRT3D_ERR_SIZE: return "DRT3D_ERR_SIZE";
+    case DRT3D_ERR_DTYPE: return "DRT3D_ERR_DTYPE";
+    case DRT3D_ERR_ALIGN: return "DRT3D_ERR_ALIGN";
+    case DRT3D_ERR_WORKSPACE: return "DRT3D_ERR_WORKSPACE";
+    case DRT3D_ERR_NOT_IN_RANGE: return "DRT3D_ERR_NOT_IN_RANGE";
+    case DRT3D_ERR_TIMEOUT: return "DRT3D_ERR_TIMEOUT";
+    case DRT3D_ERR_BOUNDS: return "DRT3D_ERR_BOUNDS";
+    case DRT3D_ERR_CUDA: return "DRT3D_ERR_CUDA";
+    case DRT3D_ERR_NO_MEMORY: return "DRT3D_ERR_NO_MEMORY";
+    }
+    return "DRT3D_ERR_UNKNOWN";
+}
+
+drt3d_status drt3d_plan_create(drt3d_plan** plan, int N, drt3d_dtype in_dtype, unsigned flags) {
+    if (!plan) return DRT3D_ERR_INVALID_ARG;
+    *plan = nullptr;
+    if (flags != 0) return DRT3D_ERR_INVALID_ARG;
+    if (N < 2 || N > kMaxN || (N & (N - 1)) != 0) return DRT3D_ERR_SIZE;
+    if (in_dtype != DRT3D_U8 && in_dtype != DRT3D_I16 && in_dtype != DRT3D_I32 && in_dtype != DRT3D_F32)
+        return DRT3D_ERR_DTYPE;
+    drt3d_plan* P = new (std::nothrow) drt3d_plan();
+    if (!P) return DRT3D_ERR_NO_MEMORY;
+    P->N = N;
+    P->n = ilog2(N);
+    P->dtype = in_dtype;
+    P->flags = flags;
+    if (cudaGetDevice(&P->device) != cudaSuccess) { delete P; return DRT3D_ERR_CUDA; }
+    if (cudaMalloc(&P->d_status, sizeof(int)) != cudaSuccess) { delete P; return DRT3D_ERR_NO_MEMORY; }
+    if (cudaMemset(P->d_status, 0, sizeof(int)) != cudaSuccess) {
+        cudaFree(P->d_status);
+        delete P;
+        return DRT3D_ERR_CUDA;
+    }
+    P->planes = make_planes_schedule(N);
+    *plan = P;
+    return DRT3D_OK;
+}
+
+drt3d_status drt3d_plan_destroy(drt3d_plan* plan) {
+    if (!plan) return DRT3D_OK;
+    if (plan->prof.events_made)
+        for (int i = 0; i < 2 * kMaxLaunch; ++i) cudaEventDestroy(plan->prof.ev[i]);
+    if (plan->d_status) cudaFree(plan->d_status);
+    delete plan;
+    return DRT3D_OK;
+}
+
+drt3d_status drt3d_planes_out_shape(const drt3d_plan* P, int64_t dims[4]) {
+    if (!P || !dims) return DRT3D_ERR_INVALID_ARG;
+    dims[0] = 12; dims[1] = P->N; dims[2] = P->N; dims[3] = 3 * (int64_t)P->N;
+    return DRT3D_OK;
+}
+
+drt3d_status drt3d_lines_out_shape(const drt3d_plan* P, int64_t dims[5]) {
+    if (!P || !dims) return DRT3D_ERR_INVALID_ARG;
+    dims[0] = 12; dims[1] = P->N; dims[2] = P->N; dims[3] = 2 * (int64_t)P->N; dims[4] = 2 * (int64_t)P->N;
+    return DRT3D_OK;
+}
+
+drt3d_status drt3d_workspace_bytes(const drt3d_plan* P, int op, size_t* bytes) {
+    if (!P || !bytes) return DRT3D_ERR_INVALID_ARG;
+    switch (op) {
+    case DRT3D_OP_PLANES_FORWARD:
+    case DRT3D_OP_PLANES_ADJOINT:
+        *bytes = (size_t)kMaxSlots * 2 * planes_buf_bytes(P);
+        return DRT3D_OK;
+    case DRT3D_OP_PLANES_INVERSE:
+    case DRT3D_OP_LINES_FORWARD:
+        *bytes = 0;
+        return DRT3D_ERR_INVALID_ARG;  // not built yet
+    }
+    return DRT3D_ERR_INVALID_ARG;
+}
+
+drt3d_status drt3d_planes_forward(const drt3d_plan* P, const void* d_in, void* d_out, uint32_t mask,
+                                  void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!P || !d_in || !d_out) return DRT3D_ERR_INVALID_ARG;
+    if (mask == 0 || (mask & ~DRT3D_ALL_DODECANTS)) return DRT3D_ERR_INVALID_ARG;
+    if (!aligned16(d_in) || !aligned16(d_out) || !aligned16(d_ws)) return DRT3D_ERR_ALIGN;
+    const size_t buf = planes_buf_bytes(P);
+    const int nslots = popcount12(mask);
+    if (!d_ws || ws_bytes < (size_t)nslots * 2 * buf) return DRT3D_ERR_WORKSPACE;
+    const int N = P->N;
+    const bool is_float = P->dtype == DRT3D_F32;
+    const size_t out_block = (size_t)N * N * 3 * N * 4;
+    const PlanesSchedule& S = P->planes;
+
+    PassLaunch L{};
+    L.N = N;
+    L.n = P->n;
+    L.dmax = 3 * N;
+    char* ws = static_cast<char*>(d_ws);
+    int mx = 0, my = 0;
+    for (int p = 0; p < S.npass; ++p) {
+        const PassSpec& ps = S.pass[p];
+        int i = 0;
+        for (int k = 0; k < 12; ++k) {
+            if (!((mask >> k) & 1)) continue;
+            char* bufA = ws + (size_t)i * 2 * buf;
+            char* bufB = bufA + buf;
+            SlotPtrs& sp = L.slot[i];
+            sp.map = dodecant_affine(N, k);
+            sp.in = (p == 0) ? d_in : ((p & 1) ? (const void*)bufA : (const void*)bufB);
+            sp.out = ps.final_ ? (void*)(static_cast<char*>(d_out) + (size_t)i * out_block)
+                               : ((p & 1) ? (void*)bufB : (void*)bufA);
+            ++i;
+        }
+        L.axis = ps.axis;
+        L.m0 = ps.m0;
+        L.gin = ps.in;
+        L.gout = ps.out;
+        L.V = warp_tile_valid(ps.G);
+        L.ntiles = (3 * N - ps.out.base + L.V - 1) / L.V;
+        L.warps = ((long long)N << (P->n - ps.G)) * L.ntiles;
+        L.accumulate = 0;
+        char nm[40];
+        std::snprintf(nm, sizeof nm, "planes_fwd_pass %c G=%d m0=%d", ps.axis ? 'y' : 'x', ps.G, ps.m0);
+        prof_begin(P, stream, nm, nslots * planes_pass_bytes(P, ps, mx, my, false));
+        if (launch_planes_pass(L, ps.G, P->dtype, ps.ingest, is_float, nslots, stream) != cudaSuccess)
+            return DRT3D_ERR_CUDA;
+        prof_end(P, stream);
+        if (ps.axis == 0) mx += ps.G; else my += ps.G;
+    }
+    return DRT3D_OK;
+}
+
+drt3d_status drt3d_planes_adjoint(const drt3d_plan* P, const void* d_cot, void* d_vol, uint32_t mask,
+                                  void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!P || !d_cot || !d_vol) return DRT3D_ERR_INVALID_ARG;
+    if (P->dtype != DRT3D_I32 && P->dtype != DRT3D_F32) return DRT3D_ERR_DTYPE;
+    if (mask == 0 || (mask & ~DRT3D_ALL_DODECANTS)) return DRT3D_ERR_INVALID_ARG;
+    if (!aligned16(d_cot) || !aligned16(d_vol) || !aligned16(d_ws)) return DRT3D_ERR_ALIGN;
+    const size_t buf = planes_buf_bytes(P);
+    const int nslots = popcount12(mask);
+    if (!d_ws || ws_bytes < (size_t)nslots * 2 * buf) return DRT3D_ERR_WORKSPACE;
+    const int N = P->N;
+    const bool is_float = P->dtype == DRT3D_F32;
+    const size_t cot_block = (size_t)N * N * 3 * N * 4;
+    const PlanesSchedule& S = P->planes;
+    char* ws = static_cast<char*>(d_ws);
+
+    PassLaunch L{};
+    L.N = N;
+    L.n = P->n;
+    L.dmax = 3 * N;
+    // Stage counts before each forward pass (for the byte accounting).
+    int mxs[kMaxPasses], mys[kMaxPasses];
+    for (int p = 0, mx = 0, my = 0; p < S.npass; ++p) {
+        mxs[p] = mx; mys[p] = my;
+        if (S.pass[p].axis == 0) mx += S.pass[p].G; else my += S.pass[p].G;
+    }
+    // Passes in reverse; q counts adjoint passes done so the ping-pong is
+    // independent of the forward parity.
+    for (int p = S.npass - 1, q = 0; p >= 0; --p, ++q) {
+        const PassSpec& ps = S.pass[p];
+        L.axis = ps.axis;
+        L.m0 = ps.m0;
+        L.gin = ps.in;
+        L.gout = ps.out;
+        L.V = warp_tile_valid(ps.G);
+        const int e_lo = (p == 0) ? 2 * N : ps.in.base;
+        const int span = 3 * N - e_lo + ((1 << ps.m0) - 1) * ((1 << ps.G) - 1);
+        L.ntiles = (span + L.V - 1) / L.V;
+        L.warps = ((long long)N << (P->n - ps.G)) * L.ntiles;
+        auto fill = [&](int i, int k) {
+            char* bufA = ws + (size_t)i * 2 * buf;
+            char* bufB = bufA + buf;
+            SlotPtrs& sp = L.slot[0 + (p == 0 ? 0 : i)];
+            sp.map = dodecant_affine(N, k);
+            sp.in = (q == 0) ? (const void*)(static_cast<const char*>(d_cot) + (size_t)i * cot_block)
+                             : ((q & 1) ? (const void*)bufA : (const void*)bufB);
+            sp.out = (p == 0) ? d_vol : ((q & 1) ? (void*)bufB : (void*)bufA);
+        };
+        if (p > 0) {
+            int i = 0;
+            for (int k = 0; k < 12; ++k)
+                if ((mask >> k) & 1) fill(i++, k);
+            L.accumulate = 0;
+            char nm[40];
+            std::snprintf(nm, sizeof nm, "planes_adj_pass %c G=%d m0=%d", ps.axis ? 'y' : 'x', ps.G, ps.m0);
+            prof_begin(P, stream, nm, nslots * planes_pass_bytes(P, ps, mxs[p], mys[p], true));
+            if (launch_planes_adjoint_pass(L, ps.G, false, is_float, nslots, stream) != cudaSuccess)
+                return DRT3D_ERR_CUDA;
+            prof_end(P, stream);
+        } else {
+            // Scatter into the volume one dodecant at a time, in increasing k,
+            // so the sum over dodecants has a fixed order.
+            int i = 0;
+            for (int k = 0; k < 12; ++k) {
+                if (!((mask >> k) & 1)) continue;
+                fill(i, k);
+                L.accumulate = (i > 0);
+                prof_begin(P, stream, "planes_adj_scatter", planes_pass_bytes(P, ps, 0, 0, true));
+                if (launch_planes_adjoint_pass(L, ps.G, true, is_float, 1, stream) != cudaSuccess)
+                    return DRT3D_ERR_CUDA;
+                prof_end(P, stream);
+                ++i;
+            }
+        }
+    }
+    return DRT3D_OK;
+}
+
+drt3d_status drt3d_planes_inverse(const drt3d_plan* P, const int32_t* d_R, int dodecant, int32_t* d_vol,
+                                  void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+    (void)d_ws; (void)ws_bytes; (void)stream;
+    if (!P || !d_R || !d_vol) return DRT3D_ERR_INVALID_ARG;
+    if (dodecant < 0 || dodecant >= 12) return DRT3D_ERR_INVALID_ARG;
+    return DRT3D_ERR_INVALID_ARG;  // not built yet
+}
+
+drt3d_status djt3d_lines_forward(const drt3d_plan* P, const void* d_in, int32_t* d_out, uint32_t mask,
+                                 void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+    (void)d_ws; (void)ws_bytes; (void)stream; (void)mask;
+    if (!P || !d_in || !d_out) return DRT3D_ERR_INVALID_ARG;
+    return DRT3D_ERR_INVALID_ARG;  // not built yet
+}
+
+drt3d_status drt3d_set_profiling(drt3d_plan* P, int enable) {
+    if (!P) return DRT3D_ERR_INVALID_ARG;
+    Profiler& pr = P->prof;
+    if (enable && !pr.events_made) {
+        for (int i = 0; i < 2 * kMaxLaunch; ++i)
+            if (cudaEventCreate(&pr.ev[i]) != cudaSuccess) return DRT3D_ERR_CUDA;
+        pr.events_made = true;
+    }
+    pr.on = enable != 0;
+    pr.count = 0;
+    return DRT3D_OK;
+}
+
+drt3d_status drt3d_profiled_launches(const drt3d_plan* P, float* ms, double* algo_bytes, int capacity, int* count) {
+    if (!P || !count) return DRT3D_ERR_INVALID_ARG;
+    const Profiler& pr = P->prof;
+    *count = pr.count;
+    if (pr.count == 0) return DRT3D_OK;
+    if (cudaEventSynchronize(pr.ev[2 * pr.count - 1]) != cudaSuccess) return DRT3D_ERR_CUDA;
+    for (int i = 0; i < pr.count && i < capacity; ++i) {
+        if (ms && cudaEventElapsedTime(&ms[i], pr.ev[2 * i], pr.ev[2 * i + 1]) != cudaSuccess)
+            return DRT3D_ERR_CUDA;
+        if (algo_bytes) algo_bytes[i] = pr.bytes[i];
+    }
+    return DRT3D_OK;
+}
+
+const char* drt3d_profiled_launch_name(const drt3d_plan* P, int i) {
+    if (!P || i < 0 || i >= P->prof.count) return "";
+    return P->prof.name[i];
+}
+
+drt3d_status drt3d_get_device_error(const drt3d_plan* P, cudaStream_t stream) {
+    if (!P) return DRT3D_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+    int h = 0;
+    if (cudaMemcpy(&h, P->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return DRT3D_ERR_CUDA;
+    if (h != 0 && cudaMemset(P->d_status, 0, sizeof(int)) != cudaSuccess) return DRT3D_ERR_CUDA;
+    return (drt3d_status)h;
+}
+
+}  // extern "C"

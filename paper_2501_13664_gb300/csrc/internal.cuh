@@ -1,0 +1,135 @@
+// internal.cuh -- shared declarations of libdrt3d's CUDA implementation.
+//
+// Buffer geometry used by every planes kernel
+// -------------------------------------------
+// The planes recursion of Algorithm 1 keeps an N x N x 3N buffer per stage.
+// Here the two half-stage axes are scheduled separately (a stage of
+// eq.(map3D) is exactly a half-stage along s1 followed by one along s2), and
+// consecutive half-stages are grouped: a pass applies G >= 1 stages along one
+// axis.  After mx stages along x and my along y, only displacements
+// d >= lo = 2N + 2 - 2^mx - 2^my can be non-zero (the volume starts at 2N and
+// every stage shifts reads upward by at most the slope-so-far plus one), so
+// an intermediate stores rows (i1, i2) over d in [base, 3N) with
+// base = lo rounded down to 8 and an 8-aligned pitch:
+//     element (i1, i2, d) at ((i1 * N + i2) * pitch + d - base).
+// Reads outside [base, 3N) are zero.  The final output uses base 0 and pitch
+// 3N, the layout of the public ABI.
+//
+// A pass of G stages along one axis, starting after m0 stages on that axis,
+// works on units (sg, w) with sg < 2^m0 (slope so far) and w < 2^(n-m0-G)
+// (remaining position bits).  The unit's 2^G input rows are
+//     a(u) = sg + (u << m0) + (w << (m0 + G)),   u < 2^G,
+// and its 2^G output rows are o(t) = t + (sg << G) + (w << (m0 + G)).
+// Unrolling eq.(digitalLine) over the G position bits gives
+//     out[o(t)][d] = sum_u in[a(u)][d + sg * u + l^G_t(u)],
+// i.e. a shear of row u by sg * u followed by a plain 2^G-point transform
+// whose shifts are compile-time constants.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "drt3d.h"
+
+namespace drt3d {
+
+constexpr int kMaxN = 1024;
+constexpr int kMaxSlots = 12;
+constexpr int kMaxPasses = 12;
+
+struct Geo {
+    int base;   // first stored displacement
+    int pitch;  // elements per row
+};
+
+// One pass of the planes schedule.
+struct PassSpec {
+    int axis;   // 0: stages along s1 (first index), 1: along s2 (second index)
+    int m0;     // stages already done along this axis
+    int G;      // stages in this pass (1..4)
+    Geo in;     // geometry read (ignored when ingest)
+    Geo out;    // geometry written
+    bool ingest;  // reads the volume through the dodecant map
+    bool final_;  // writes the public output layout
+};
+
+struct PlanesSchedule {
+    int npass;
+    PassSpec pass[kMaxPasses];
+    size_t buf_elems;  // elements of the largest intermediate (one buffer)
+};
+
+// Affine map from a frame coordinate (x', y', z') to a flat index of the
+// original volume: o0 + x' sx + y' sy + z' sz.
+struct Affine {
+    long long o0, sx, sy, sz;
+};
+
+// Dodecant k's frame (Algorithm 2's InOrder, see drt3d.h) and sector k's
+// frame (Section 4.1), as affine maps for an N^3 volume.
+Affine dodecant_affine(int N, int k);
+Affine sector_affine(int N, int k);
+
+// Planes schedule for N: the n stages of each axis are split into groups of
+// at most 4 and the passes alternate x, y, x, y, ...
+PlanesSchedule make_planes_schedule(int N);
+
+inline int ilog2(int N) {
+    int n = 0;
+    while ((1 << n) < N) ++n;
+    return n;
+}
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Per-dodecant pointers of one pass launch.
+struct SlotPtrs {
+    const void* in;
+    void* out;
+    Affine map;
+};
+
+struct PassLaunch {
+    SlotPtrs slot[kMaxSlots];
+    int N, n;
+    int axis, m0;
+    Geo gin, gout;
+    int dmax;             // 3N
+    int V;                // valid outputs per warp tile
+    int ntiles;           // warp tiles along d
+    long long warps;      // warps per slot
+    int accumulate;       // adjoint scatter: 0 = store, 1 = add
+};
+
+// Launchers (implemented per .cu file); return cudaGetLastError().
+cudaError_t launch_planes_pass(const PassLaunch& L, int G, drt3d_dtype in_dtype, bool ingest,
+                               bool is_float, int nslots, cudaStream_t s);
+cudaError_t launch_planes_adjoint_pass(const PassLaunch& L, int G, bool scatter, bool is_float,
+                                       int nslots, cudaStream_t s);
+
+}  // namespace drt3d
+
+namespace drt3d {
+constexpr int kMaxLaunch = 2048;
+struct Profiler {
+    bool on = false;
+    bool events_made = false;
+    int count = 0;
+    cudaEvent_t ev[2 * kMaxLaunch];
+    double bytes[kMaxLaunch];
+    char name[kMaxLaunch][40];
+};
+}  // namespace drt3d
+
+struct drt3d_plan {
+    mutable drt3d::Profiler prof;
+    int N;
+    int n;
+    drt3d_dtype dtype;
+    unsigned flags;
+    int device;
+    int* d_status;  // device status word (drt3d_status), 0 = OK
+    drt3d::PlanesSchedule planes;
+};

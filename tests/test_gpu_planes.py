@@ -1,0 +1,141 @@
+"""GPU parity of the planes forward and adjoint against the CPU oracle.
+
+Integer results must be bit-exact (wrapping int32).  Float32 results are held
+to the per-cell bound |R_gpu - R_fp64| <= 1e-5 * (A|x|)_cell, the relative
+tolerance of the differentiable path, scaled by the sum of magnitudes that
+enter the cell (a plain per-cell relative bound is ill-posed where sums
+cancel).
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+FTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def drt():
+    import paper_2501_13664_gb300 as drt3d
+
+    return drt3d
+
+
+def _fwd(drt, f, dodecants=0xFFF):
+    return drt.planes_forward(torch.from_numpy(np.ascontiguousarray(f)).cuda(), dodecants).cpu().numpy()
+
+
+@pytest.mark.parametrize("N", [2, 4, 8, 16, 32])
+@pytest.mark.parametrize("dt", ["u8", "i16", "i32"])
+def test_forward_integer_exact(drt, oracle_mod, N, dt):
+    if dt == "u8":
+        f = synth.random_int32((N, N, N), N, 0, 256).astype(np.uint8)
+    elif dt == "i16":
+        f = synth.random_int32((N, N, N), N + 1, -32768, 32768).astype(np.int16)
+    else:
+        f = synth.random_int32((N, N, N), N + 2)  # full range: sums wrap
+    np.testing.assert_array_equal(_fwd(drt, f), oracle_mod.planes_forward(f))
+
+
+@pytest.mark.parametrize("mask", [0x001, 0x800, 0x0A5, 0xF0F])
+def test_forward_dodecant_subsets(drt, oracle_mod, mask):
+    N = 16
+    f = synth.random_int32((N, N, N), 3, 0, 256)
+    ks = [k for k in range(12) if (mask >> k) & 1]
+    np.testing.assert_array_equal(_fwd(drt, f, mask), oracle_mod.planes_forward(f, ks))
+
+
+def test_config_c1_bit_exact_vs_definition_and_recursion(drt, oracle_mod):
+    f = synth.c1_volume()
+    got = _fwd(drt, f)
+    np.testing.assert_array_equal(got, oracle_mod.planes_forward(f))
+    np.testing.assert_array_equal(got, oracle_mod.planes_forward(f, exact="brute"))
+
+
+@pytest.mark.parametrize("N", [64, 128])
+def test_forward_mid_sizes_exact(drt, oracle_mod, N):
+    f = synth.c2_volume(N, seed=N)
+    np.testing.assert_array_equal(_fwd(drt, f), oracle_mod.planes_forward(f))
+
+
+def test_config_c2_full_size(drt, oracle_mod):
+    """N = 256 uint8 sparse volume with embedded planes: two dodecants in full
+    against Algorithm 1, 10^5 random cells against the definition over all
+    twelve, and the mass invariant on every slope pair."""
+    N = 256
+    f = synth.c2_volume(N)
+    R = drt.planes_forward(torch.from_numpy(f).cuda())
+    total = int(f.astype(np.int64).sum())
+    mass = R.to(torch.int64).sum(dim=3)
+    assert bool((mass == total).all())
+    assert bool((R[:, :, :, :2] == 0).all())
+    for k in (0, 5):
+        np.testing.assert_array_equal(R[k].cpu().numpy(), oracle_mod.planes_forward(f, [k])[0])
+    rng = np.random.default_rng(123)
+    Rc = R.cpu().numpy()
+    per = 100_000 // 12 + 1
+    for k in range(12):
+        g = oracle_mod.dodecant_volume(f.astype(np.int32), k)
+        s1 = rng.integers(0, N, per)
+        s2 = rng.integers(0, N, per)
+        d = rng.integers(0, 3 * N, per)
+        for a, b, c in zip(s1, s2, d):
+            assert oracle_mod.planes_cell(g, int(a), int(b), int(c)) == int(Rc[k, a, b, c])
+
+
+@pytest.mark.parametrize("N", [4, 16, 64])
+def test_forward_float_within_tolerance(drt, oracle_mod, N):
+    x = synth.random_float((N, N, N), 7)
+    got = _fwd(drt, x).astype(np.float64)
+    ref = oracle_mod.planes_forward(x.astype(np.float64))
+    mag = oracle_mod.planes_forward(np.abs(x).astype(np.float64))
+    assert np.all(np.abs(got - ref) <= FTOL * mag + 1e-30)
+
+
+@pytest.mark.parametrize("N", [2, 8, 32])
+def test_adjoint_integer_exact(drt, oracle_mod, N):
+    r = synth.random_int32((12, N, N, 3 * N), 11)
+    got = drt.planes_adjoint(torch.from_numpy(r).cuda()).cpu().numpy()
+    np.testing.assert_array_equal(got, oracle_mod.planes_adjoint(r))
+
+
+def test_adjoint_subset_order(drt, oracle_mod):
+    N = 16
+    ks = [1, 4, 9]
+    r = synth.random_int32((3, N, N, 3 * N), 12, -1000, 1000)
+    got = drt.planes_adjoint(torch.from_numpy(r).cuda(), ks).cpu().numpy()
+    np.testing.assert_array_equal(got, oracle_mod.planes_adjoint(r, ks))
+
+
+@pytest.mark.parametrize("N", [8, 64])
+def test_adjoint_float_within_tolerance(drt, oracle_mod, N):
+    r = synth.random_float((12, N, N, 3 * N), 13)
+    got = drt.planes_adjoint(torch.from_numpy(r).cuda()).cpu().numpy().astype(np.float64)
+    ref = oracle_mod.planes_adjoint(r.astype(np.float64))
+    mag = oracle_mod.planes_adjoint(np.abs(r).astype(np.float64))
+    assert np.all(np.abs(got - ref) <= FTOL * mag + 1e-30)
+
+
+def test_adjoint_is_deterministic(drt):
+    N = 32
+    r = torch.from_numpy(synth.random_float((12, N, N, 3 * N), 14)).cuda()
+    a = drt.planes_adjoint(r)
+    b = drt.planes_adjoint(r)
+    assert torch.equal(a, b)
+
+
+def test_argument_errors_raise(drt):
+    f = torch.zeros((8, 8, 8), dtype=torch.int32, device="cuda")
+    with pytest.raises(ValueError):
+        drt.planes_forward(f, 0)
+    with pytest.raises(ValueError):
+        drt.planes_forward(torch.zeros((8, 8, 4), dtype=torch.int32, device="cuda"))
+    plan = drt.get_plan(8, torch.int32)
+    out = torch.empty((12, 8, 8, 24), dtype=torch.int32, device="cuda")
+    ws = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(drt.DRT3DError):
+        drt.planes_forward(f, 0xFFF, out=out, workspace=ws)
+    assert plan.device_error() == 0
