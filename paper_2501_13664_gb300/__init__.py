@@ -167,6 +167,39 @@ def planes_adjoint(cot: torch.Tensor, dodecants=ALL, out: torch.Tensor | None = 
     return out.to("cpu") if host else out
 
 
+class NotInRangeError(DRT3DError):
+    """The array handed to ``planes_inverse`` is not a forward transform."""
+
+
+def planes_inverse(R_k: torch.Tensor, dodecant: int, out: torch.Tensor | None = None,
+                   workspace: torch.Tensor | None = None, check: bool = True) -> torch.Tensor:
+    """Exact integer inverse of one dodecant's transform -> (N, N, N) int32.
+
+    With ``check`` the call synchronises and raises ``NotInRangeError`` when
+    ``R_k`` is not in the range of the forward map; without it the status
+    stays in the plan's device word (``get_plan(N, torch.int32).device_error()``).
+    """
+    R_d, host = _to_device(R_k)
+    if R_d.dtype != torch.int32 or R_d.dim() != 3 or R_d.shape[2] != 3 * R_d.shape[0]:
+        raise ValueError(f"expected an (N, N, 3N) int32 block, got {tuple(R_d.shape)} {R_d.dtype}")
+    N = int(R_d.shape[0])
+    if not 0 <= int(dodecant) < 12:
+        raise ValueError(f"dodecant index out of range: {dodecant}")
+    plan = get_plan(N, torch.int32)
+    if out is None:
+        out = torch.empty((N, N, N), dtype=torch.int32, device=R_d.device)
+    ws = workspace if workspace is not None else plan.workspace("planes_inverse")
+    _abi.check(plan._lib.drt3d_planes_inverse(plan.handle, R_d.data_ptr(), int(dodecant), out.data_ptr(),
+                                              ws.data_ptr(), ws.numel(), _stream()),
+               "drt3d_planes_inverse")
+    if check:
+        code = plan.device_error()
+        if code == 6:
+            raise NotInRangeError(code, "drt3d_planes_inverse")
+        _abi.check(code, "drt3d_planes_inverse (device)")
+    return out.to("cpu") if host else out
+
+
 class PlanesTransform(torch.autograd.Function):
     """Differentiable 3D DRT of planes for float32 volumes.
 

@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
 
 #include "internal.cuh"
@@ -90,6 +91,110 @@ PlanesSchedule make_planes_schedule(int N) {
     return S;
 }
 
+static ElemKind kind_of(drt3d_dtype d) {
+    switch (d) {
+    case DRT3D_U8: return ElemKind::U8;
+    case DRT3D_I16: return ElemKind::I16;
+    case DRT3D_I32: return ElemKind::I32;
+    default: return ElemKind::F32;
+    }
+}
+
+FusedSchedule make_fused_schedule(int N, drt3d_dtype dtype) {
+    FusedSchedule S{};
+    const int n = ilog2(N);
+    const int ng = (n + 3) / 4;
+    int m = 0;
+    size_t maxb = 0;
+    for (int g = 0; g < ng; ++g) {
+        FusedPass& P = S.pass[g];
+        P.G = n / ng + (g < n % ng ? 1 : 0);
+        P.m0 = m;
+        P.ingest = (g == 0);
+        P.in = (g == 0) ? Geo{0, 0} : S.pass[g - 1].out;
+        P.in_kind = (g == 0) ? kind_of(dtype) : S.pass[g - 1].out_kind;
+        m += P.G;
+        P.final_ = (g == ng - 1);
+        if (P.final_) {
+            P.out = Geo{0, 3 * N};
+            P.out_kind = dtype == DRT3D_F32 ? ElemKind::F32 : ElemKind::I32;
+        } else {
+            P.out = planes_geo(N, m, m);
+            // u8 volumes: every intermediate value is a sum of 4^m voxels of at
+            // most 255, so it is exact in 16 bits while 255 * 4^m < 2^16.
+            if (dtype == DRT3D_U8 && 255L * (1L << (2 * m)) <= 65535L) P.out_kind = ElemKind::U16;
+            else P.out_kind = dtype == DRT3D_F32 ? ElemKind::F32 : ElemKind::I32;
+            const size_t b = align_up((size_t)N * N * P.out.pitch * elem_bytes(P.out_kind), 256);
+            if (b > maxb) maxb = b;
+        }
+    }
+    S.npass = ng;
+    S.buf_bytes = maxb;
+    return S;
+}
+
+// Ingest mode of dodecant k's first pass (see planes_fused.cu).
+static void ingest_mode(int N, const Affine& A, FusedSlot& fs) {
+    fs.swap = 0;
+    fs.reverse = 0;
+    fs.mode = kIngestGeneric;
+    if (N >= 4 && (A.sz == 1 || A.sz == -1)) {
+        fs.mode = kIngestZ;
+        fs.reverse = A.sz < 0;
+    } else if (A.sx == 1 || A.sx == -1) {
+        fs.mode = kIngestRun;
+        fs.reverse = A.sx < 0;
+    } else if (A.sy == 1 || A.sy == -1) {
+        fs.mode = kIngestRun;
+        fs.swap = 1;
+        fs.reverse = A.sy < 0;
+    }
+}
+
+// Exact-inverse schedule: per axis the n stages are undone in groups of at
+// most Gmax (so a unit's rows over the full 3N range fit in shared memory),
+// last group first, the s2 axis before the s1 axis within each group.
+struct InvStep { int axis, G, m0, mx_in, my_in, mx_out, my_out; };
+static int inverse_steps(int N, InvStep* steps) {
+    const int n = ilog2(N);
+    const int gmax = N <= 512 ? 4 : 3;
+    const int ng = (n + gmax - 1) / gmax;
+    int sz[12], M[13];
+    M[0] = 0;
+    for (int g = 0; g < ng; ++g) {
+        sz[g] = n / ng + (g < n % ng ? 1 : 0);
+        M[g + 1] = M[g] + sz[g];
+    }
+    int c = 0;
+    for (int g = ng - 1; g >= 0; --g) {
+        steps[c++] = InvStep{1, sz[g], M[g], M[g + 1], M[g + 1], M[g + 1], M[g]};
+        steps[c++] = InvStep{0, sz[g], M[g], M[g + 1], M[g], M[g], M[g]};
+    }
+    return c;
+}
+
+// Inverse intermediates: base rounded down to 32 so that (for N >= 32) rows
+// are whole 32-element chunks of the inverse kernel.
+static Geo inv_geo(int N, int mx, int my) {
+    if (mx == ilog2(N) && my == ilog2(N)) return Geo{0, 3 * N};
+    const int lo = 2 * N + 2 - (1 << mx) - (1 << my);
+    Geo g;
+    g.base = lo & ~31;
+    g.pitch = (int)align_up((size_t)(3 * N - g.base), 8);
+    return g;
+}
+
+static size_t inverse_buf_bytes(int N) {
+    InvStep st[24];
+    const int c = inverse_steps(N, st);
+    size_t mx = 0;
+    for (int i = 0; i + 1 < c; ++i) {
+        const Geo g = inv_geo(N, st[i].mx_out, st[i].my_out);
+        mx = std::max(mx, align_up((size_t)N * N * g.pitch * 4, 256));
+    }
+    return mx;
+}
+
 static size_t planes_buf_bytes(const drt3d_plan* P) {
     return align_up(P->planes.buf_elems * 4, 256);
 }
@@ -133,6 +238,19 @@ static double planes_pass_bytes(const drt3d_plan* P, const PassSpec& ps, int mx0
     const double vol = N * N * N * (ps.ingest ? item : 4.0);
     const double in_b = ps.ingest ? vol : N * N * (3 * N - lo_in) * 4.0;
     const double out_b = ps.final_ ? N * N * 3 * N * 4.0 : N * N * (3 * N - lo_out) * 4.0;
+    return in_b + out_b;
+}
+
+// Algorithmic bytes of one fused pass for one dodecant (compact rows read at
+// their element size, or the volume; rows written at their element size).
+static double fused_pass_bytes(const drt3d_plan* P, const FusedPass& ps) {
+    const double N = P->N;
+    const int m1 = ps.m0 + ps.G;
+    const double lo_in = 2 * N + 2 - 2.0 * (1 << ps.m0);
+    const double lo_out = 2 * N + 2 - 2.0 * (1 << m1);
+    const double in_b = ps.ingest ? N * N * N * elem_bytes(ps.in_kind)
+                                  : N * N * (3 * N - lo_in) * elem_bytes(ps.in_kind);
+    const double out_b = ps.final_ ? N * N * 3 * N * 4.0 : N * N * (3 * N - lo_out) * elem_bytes(ps.out_kind);
     return in_b + out_b;
 }
 
@@ -182,6 +300,7 @@ drt3d_status drt3d_plan_create(drt3d_plan** plan, int N, drt3d_dtype in_dtype, u
         return DRT3D_ERR_CUDA;
     }
     P->planes = make_planes_schedule(N);
+    P->fused = make_fused_schedule(N, in_dtype);
     *plan = P;
     return DRT3D_OK;
 }
@@ -212,9 +331,11 @@ drt3d_status drt3d_workspace_bytes(const drt3d_plan* P, int op, size_t* bytes) {
     switch (op) {
     case DRT3D_OP_PLANES_FORWARD:
     case DRT3D_OP_PLANES_ADJOINT:
-        *bytes = (size_t)kMaxSlots * 2 * planes_buf_bytes(P);
+        *bytes = (size_t)kMaxSlots * 2 * (op == DRT3D_OP_PLANES_FORWARD ? P->fused.buf_bytes : planes_buf_bytes(P));
         return DRT3D_OK;
     case DRT3D_OP_PLANES_INVERSE:
+        *bytes = 2 * inverse_buf_bytes(P->N);
+        return DRT3D_OK;
     case DRT3D_OP_LINES_FORWARD:
         *bytes = 0;
         return DRT3D_ERR_INVALID_ARG;  // not built yet
@@ -227,49 +348,46 @@ drt3d_status drt3d_planes_forward(const drt3d_plan* P, const void* d_in, void* d
     if (!P || !d_in || !d_out) return DRT3D_ERR_INVALID_ARG;
     if (mask == 0 || (mask & ~DRT3D_ALL_DODECANTS)) return DRT3D_ERR_INVALID_ARG;
     if (!aligned16(d_in) || !aligned16(d_out) || !aligned16(d_ws)) return DRT3D_ERR_ALIGN;
-    const size_t buf = planes_buf_bytes(P);
+    const FusedSchedule& S = P->fused;
+    const size_t buf = S.buf_bytes;
     const int nslots = popcount12(mask);
-    if (!d_ws || ws_bytes < (size_t)nslots * 2 * buf) return DRT3D_ERR_WORKSPACE;
+    if (S.npass > 1 && (!d_ws || ws_bytes < (size_t)nslots * 2 * buf)) return DRT3D_ERR_WORKSPACE;
     const int N = P->N;
-    const bool is_float = P->dtype == DRT3D_F32;
     const size_t out_block = (size_t)N * N * 3 * N * 4;
-    const PlanesSchedule& S = P->planes;
-
-    PassLaunch L{};
+    char* ws = static_cast<char*>(d_ws);
+    FusedLaunch L{};
     L.N = N;
     L.n = P->n;
     L.dmax = 3 * N;
-    char* ws = static_cast<char*>(d_ws);
-    int mx = 0, my = 0;
     for (int p = 0; p < S.npass; ++p) {
-        const PassSpec& ps = S.pass[p];
+        const FusedPass& ps = S.pass[p];
         int i = 0;
         for (int k = 0; k < 12; ++k) {
             if (!((mask >> k) & 1)) continue;
             char* bufA = ws + (size_t)i * 2 * buf;
             char* bufB = bufA + buf;
-            SlotPtrs& sp = L.slot[i];
-            sp.map = dodecant_affine(N, k);
-            sp.in = (p == 0) ? d_in : ((p & 1) ? (const void*)bufA : (const void*)bufB);
-            sp.out = ps.final_ ? (void*)(static_cast<char*>(d_out) + (size_t)i * out_block)
+            FusedSlot& fs = L.slot[i];
+            fs.map = dodecant_affine(N, k);
+            ingest_mode(N, fs.map, fs);
+            fs.in = (p == 0) ? d_in : ((p & 1) ? (const void*)bufA : (const void*)bufB);
+            fs.out = ps.final_ ? (void*)(static_cast<char*>(d_out) + (size_t)i * out_block)
                                : ((p & 1) ? (void*)bufB : (void*)bufA);
             ++i;
         }
-        L.axis = ps.axis;
         L.m0 = ps.m0;
         L.gin = ps.in;
         L.gout = ps.out;
-        L.V = warp_tile_valid(ps.G);
+        L.V = fused_valid(ps.G);
         L.ntiles = (3 * N - ps.out.base + L.V - 1) / L.V;
-        L.warps = ((long long)N << (P->n - ps.G)) * L.ntiles;
-        L.accumulate = 0;
+        const long long per_axis = 1LL << (P->n - ps.G);
+        L.ctas = per_axis * per_axis * L.ntiles;
+        L.vec_store = (ps.out.pitch % 4 == 0) && (ps.out.base % 4 == 0);
         char nm[40];
-        std::snprintf(nm, sizeof nm, "planes_fwd_pass %c G=%d m0=%d", ps.axis ? 'y' : 'x', ps.G, ps.m0);
-        prof_begin(P, stream, nm, nslots * planes_pass_bytes(P, ps, mx, my, false));
-        if (launch_planes_pass(L, ps.G, P->dtype, ps.ingest, is_float, nslots, stream) != cudaSuccess)
+        std::snprintf(nm, sizeof nm, "planes_fused G=%d m0=%d", ps.G, ps.m0);
+        prof_begin(P, stream, nm, nslots * fused_pass_bytes(P, ps));
+        if (launch_planes_fused(L, ps.G, ps.in_kind, ps.out_kind, ps.ingest, nslots, stream) != cudaSuccess)
             return DRT3D_ERR_CUDA;
         prof_end(P, stream);
-        if (ps.axis == 0) mx += ps.G; else my += ps.G;
     }
     return DRT3D_OK;
 }
@@ -353,10 +471,41 @@ drt3d_status drt3d_planes_adjoint(const drt3d_plan* P, const void* d_cot, void* 
 
 drt3d_status drt3d_planes_inverse(const drt3d_plan* P, const int32_t* d_R, int dodecant, int32_t* d_vol,
                                   void* d_ws, size_t ws_bytes, cudaStream_t stream) {
-    (void)d_ws; (void)ws_bytes; (void)stream;
     if (!P || !d_R || !d_vol) return DRT3D_ERR_INVALID_ARG;
     if (dodecant < 0 || dodecant >= 12) return DRT3D_ERR_INVALID_ARG;
-    return DRT3D_ERR_INVALID_ARG;  // not built yet
+    if (P->dtype == DRT3D_F32) return DRT3D_ERR_DTYPE;
+    if (!aligned16(d_R) || !aligned16(d_vol) || !aligned16(d_ws)) return DRT3D_ERR_ALIGN;
+    const int N = P->N;
+    const size_t buf = inverse_buf_bytes(N);
+    InvStep st[24];
+    const int c = inverse_steps(N, st);
+    if (c > 1 && (!d_ws || ws_bytes < 2 * buf)) return DRT3D_ERR_WORKSPACE;
+    char* ws = static_cast<char*>(d_ws);
+    InvLaunch L{};
+    L.status = P->d_status;
+    L.map = dodecant_affine(N, dodecant);
+    L.N = N;
+    L.n = P->n;
+    L.dmax = 3 * N;
+    for (int i = 0; i < c; ++i) {
+        const InvStep& t = st[i];
+        L.axis = t.axis;
+        L.m0 = t.m0;
+        L.gin = inv_geo(N, t.mx_in, t.my_in);
+        L.gout = inv_geo(N, t.mx_out, t.my_out);
+        L.lo_out = 2 * N + 2 - (1 << t.mx_out) - (1 << t.my_out);
+        L.scatter = (i == c - 1);
+        L.in = (i == 0) ? (const void*)d_R : (const void*)(ws + (size_t)((i - 1) & 1) * buf);
+        L.out = L.scatter ? (void*)d_vol : (void*)(ws + (size_t)(i & 1) * buf);
+        char nm[40];
+        std::snprintf(nm, sizeof nm, "planes_inv_pass %c G=%d m0=%d", t.axis ? 'y' : 'x', t.G, t.m0);
+        const double W = 3.0 * N - L.gin.base;
+        const double outb = L.scatter ? (double)N * N * N * 4 : (double)N * N * (3.0 * N - L.lo_out) * 4;
+        prof_begin(P, stream, nm, (double)N * N * W * 4 + outb);
+        if (launch_planes_inverse_pass(L, t.G, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+        prof_end(P, stream);
+    }
+    return DRT3D_OK;
 }
 
 drt3d_status djt3d_lines_forward(const drt3d_plan* P, const void* d_in, int32_t* d_out, uint32_t mask,

@@ -103,7 +103,74 @@ struct PassLaunch {
     int accumulate;       // adjoint scatter: 0 = store, 1 = add
 };
 
+// Element type of a buffer read or written by a fused pass.
+enum class ElemKind : int { U8 = 0, I16 = 1, I32 = 2, F32 = 3, U16 = 4 };
+inline int elem_bytes(ElemKind k) {
+    return k == ElemKind::U8 ? 1 : (k == ElemKind::I16 || k == ElemKind::U16) ? 2 : 4;
+}
+
+// How the first fused pass reads the volume for one dodecant.
+constexpr int kIngestGeneric = 0;  // scalar gathers
+constexpr int kIngestZ = 1;        // the frame's z' axis is contiguous in memory
+constexpr int kIngestRun = 2;      // the phase-1 axis is contiguous in memory
+
+struct FusedSlot {
+    const void* in;
+    void* out;
+    Affine map;
+    int swap;     // 1: phase 1 runs along the second frame axis (y')
+    int mode;     // kIngest* (first pass only)
+    int reverse;  // the contiguous axis runs backwards in memory
+};
+
+struct FusedLaunch {
+    FusedSlot slot[kMaxSlots];
+    int N, n;
+    int m0;          // stages already done on each axis
+    Geo gin, gout;
+    int dmax;        // 3N
+    int V;           // valid displacements per CTA tile
+    int ntiles;
+    long long ctas;  // CTAs per slot
+    int vec_store;   // output rows allow aligned vector stores
+};
+
+// One fused pass: G stages of eq.(map3D) (both axes).
+struct FusedPass {
+    int G, m0;
+    Geo in, out;
+    ElemKind in_kind, out_kind;
+    bool ingest, final_;
+};
+
+struct FusedSchedule {
+    int npass;
+    FusedPass pass[8];
+    size_t buf_bytes;  // bytes of one intermediate buffer (256-aligned)
+};
+
+FusedSchedule make_fused_schedule(int N, drt3d_dtype dtype);
+
 // Launchers (implemented per .cu file); return cudaGetLastError().
+// One pass of the exact inverse: undo G half-stages along one axis.
+struct InvLaunch {
+    const void* in;   // rows of the later stage (geometry gin)
+    void* out;        // rows of the earlier stage (geometry gout) or the volume
+    int* status;      // device status word
+    Affine map;       // dodecant map (scatter pass)
+    int N, n;
+    int axis, m0;     // axis undone; stages on that axis before the group
+    Geo gin, gout;
+    int dmax;         // 3N
+    int lo_out;       // values below this displacement must vanish after the pass
+    int scatter;      // last pass: write the volume through the dodecant map
+};
+size_t inverse_smem_bytes(int N, int G, int base);
+cudaError_t launch_planes_inverse_pass(const InvLaunch& L, int G, cudaStream_t s);
+
+int fused_valid(int G);  // valid displacements per CTA tile of a G-stage fused pass
+cudaError_t launch_planes_fused(const FusedLaunch& L, int G, ElemKind in_kind, ElemKind out_kind,
+                                bool ingest, int nslots, cudaStream_t s);
 cudaError_t launch_planes_pass(const PassLaunch& L, int G, drt3d_dtype in_dtype, bool ingest,
                                bool is_float, int nslots, cudaStream_t s);
 cudaError_t launch_planes_adjoint_pass(const PassLaunch& L, int G, bool scatter, bool is_float,
@@ -131,5 +198,6 @@ struct drt3d_plan {
     unsigned flags;
     int device;
     int* d_status;  // device status word (drt3d_status), 0 = OK
-    drt3d::PlanesSchedule planes;
+    drt3d::PlanesSchedule planes;  // one-axis passes (adjoint)
+    drt3d::FusedSchedule fused;    // two-axis passes (forward)
 };

@@ -133,9 +133,11 @@ def test_argument_errors_raise(drt):
         drt.planes_forward(f, 0)
     with pytest.raises(ValueError):
         drt.planes_forward(torch.zeros((8, 8, 4), dtype=torch.int32, device="cuda"))
-    plan = drt.get_plan(8, torch.int32)
-    out = torch.empty((12, 8, 8, 24), dtype=torch.int32, device="cuda")
+    # N = 64 runs two passes and needs an intermediate workspace
+    g = torch.zeros((64, 64, 64), dtype=torch.int32, device="cuda")
+    plan = drt.get_plan(64, torch.int32)
+    out = torch.empty((12, 64, 64, 192), dtype=torch.int32, device="cuda")
     ws = torch.empty(16, dtype=torch.uint8, device="cuda")
     with pytest.raises(drt.DRT3DError):
-        drt.planes_forward(f, 0xFFF, out=out, workspace=ws)
+        drt.planes_forward(g, 0xFFF, out=out, workspace=ws)
     assert plan.device_error() == 0
