@@ -68,7 +68,8 @@ typedef enum drt3d_status {
     DRT3D_ERR_TIMEOUT = 7,      /* a bounded device-side wait gave up */
     DRT3D_ERR_BOUNDS = 8,       /* a device-side bounds check failed */
     DRT3D_ERR_CUDA = 9,         /* a CUDA runtime call failed */
-    DRT3D_ERR_NO_MEMORY = 10    /* host allocation or plan status word failed */
+    DRT3D_ERR_NO_MEMORY = 10,   /* host allocation or plan status word failed */
+    DRT3D_ERR_SCRATCH_LIMIT = 11 /* call needs more than the fixed no-alloc scratch */
 } drt3d_status;
 
 typedef enum drt3d_dtype {
@@ -182,6 +183,33 @@ drt3d_status drt3d_profiled_launches(const drt3d_plan* plan, float* ms, double* 
                                      int* count);
 /* Name of recorded launch i ("" if out of range). */
 const char* drt3d_profiled_launch_name(const drt3d_plan* plan, int i);
+
+/* Forward planes transform that allocates nothing and takes no workspace.
+ * The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory where they run the transform (host callbacks or
+ * real-time loops that must stay out of the allocator, plug-in hosts that
+ * hand out only input and output buffers, processes whose device memory is
+ * reserved up front by another framework).  Same arguments, layouts and
+ * results as drt3d_planes_forward, minus the workspace.
+ *   Scratch: a fixed library-owned device array of
+ *            drt3d_noalloc_scratch_bytes() = 16 MiB, held by every GPU on
+ *            which the library is loaded until the process exits.  A call
+ *            needing more (two intermediate buffers per selected dodecant,
+ *            e.g. all 12 dodecants at N = 64 with 32-bit input or at N >= 128)
+ *            returns DRT3D_ERR_SCRATCH_LIMIT without enqueuing anything;
+ *            N <= 16 needs none.
+ *   Set-up:  the first call on a device looks up the array's device address
+ *            (cudaGetSymbolAddress) and caches it; make that first call
+ *            before any stream capture.
+ *   Sharing: all calls use the same array and nothing in it must start at
+ *            zero (every element is written before it is read), but calls
+ *            that overlap on the GPU race on it: serialise them.
+ * Errors: INVALID_ARG, ALIGN, SCRATCH_LIMIT, CUDA. */
+drt3d_status drt3d_planes_forward_noalloc(const drt3d_plan* plan, const void* d_in, void* d_out,
+                                          uint32_t dodecant_mask, cudaStream_t stream);
+
+/* Size in bytes of the fixed scratch used by drt3d_planes_forward_noalloc. */
+size_t drt3d_noalloc_scratch_bytes(void);
 
 /* Library version, major * 10000 + minor * 100 + patch. */
 int drt3d_version(void);

@@ -38,12 +38,15 @@ SIGNATURES = {
                                     ctypes.POINTER(I)]),
     "drt3d_profiled_launch_name": (ctypes.c_char_p, [P, I]),
     "drt3d_version": (I, []),
+    "drt3d_planes_forward_noalloc": (I, [P, P, P, U32, P]),
+    "drt3d_noalloc_scratch_bytes": (SZ, []),
 }
 
 STATUS = {
     0: "DRT3D_OK", 1: "DRT3D_ERR_INVALID_ARG", 2: "DRT3D_ERR_SIZE", 3: "DRT3D_ERR_DTYPE",
     4: "DRT3D_ERR_ALIGN", 5: "DRT3D_ERR_WORKSPACE", 6: "DRT3D_ERR_NOT_IN_RANGE",
     7: "DRT3D_ERR_TIMEOUT", 8: "DRT3D_ERR_BOUNDS", 9: "DRT3D_ERR_CUDA", 10: "DRT3D_ERR_NO_MEMORY",
+    11: "DRT3D_ERR_SCRATCH_LIMIT",
 }
 DTYPES = {"u8": 0, "i16": 1, "i32": 2, "f32": 3}
 OPS = {"planes_forward": 0, "planes_adjoint": 1, "planes_inverse": 2, "lines_forward": 3}

@@ -275,6 +275,7 @@ const char* drt3d_status_string(drt3d_status s) {
     case DRT3D_ERR_BOUNDS: return "DRT3D_ERR_BOUNDS";
     case DRT3D_ERR_CUDA: return "DRT3D_ERR_CUDA";
     case DRT3D_ERR_NO_MEMORY: return "DRT3D_ERR_NO_MEMORY";
+    case DRT3D_ERR_SCRATCH_LIMIT: return "DRT3D_ERR_SCRATCH_LIMIT";
     }
     return "DRT3D_ERR_UNKNOWN";
 }
