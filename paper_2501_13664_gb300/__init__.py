@@ -200,6 +200,24 @@ def planes_inverse(R_k: torch.Tensor, dodecant: int, out: torch.Tensor | None = 
     return out.to("cpu") if host else out
 
 
+def lines_forward(vol: torch.Tensor, sectors=ALL, out: torch.Tensor | None = None,
+                  workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """Forward 3D DJT of lines over the selected sectors (Algorithm 3)."""
+    vol_d, host = _to_device(vol)
+    N = _vol_check(vol_d)
+    if vol_d.dtype == torch.float32:
+        raise TypeError("the lines transform takes integer volumes")
+    m = _mask(sectors)
+    plan = get_plan(N, vol_d.dtype)
+    if out is None:
+        out = torch.empty((_count(m), N, N, 2 * N, 2 * N), dtype=torch.int32, device=vol_d.device)
+    ws = workspace if workspace is not None else plan.workspace("lines_forward")
+    _abi.check(plan._lib.djt3d_lines_forward(plan.handle, vol_d.data_ptr(), out.data_ptr(), m,
+                                             ws.data_ptr(), ws.numel(), _stream()),
+               "djt3d_lines_forward")
+    return out.to("cpu") if host else out
+
+
 class PlanesTransform(torch.autograd.Function):
     """Differentiable 3D DRT of planes for float32 volumes.
 

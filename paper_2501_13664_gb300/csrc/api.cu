@@ -195,6 +195,25 @@ static size_t inverse_buf_bytes(int N) {
     return mx;
 }
 
+// Lines schedule: n <= 4 in one pass, else two passes (ceil(n/2), floor(n/2)),
+// the larger first so that the last (output-writing) pass keeps G <= 3 and
+// one warp tile spans a whole output row where possible.
+static int djt_groups(int N, int* G) {
+    const int n = ilog2(N);
+    if (n <= 4) { G[0] = n; return 1; }
+    G[0] = (n + 1) / 2;
+    G[1] = n / 2;
+    return 2;
+}
+static int djt_base(int N, int m) { return (N + 1 - (1 << m)) & ~3; }
+static size_t djt_buf_bytes(int N) {
+    int G[2];
+    if (djt_groups(N, G) < 2) return 0;
+    const int n = ilog2(N), m = G[0];
+    const long long pitch = 2LL * N - djt_base(N, m);
+    return align_up((size_t)(1LL << (n + m)) * pitch * pitch * 4, 256);
+}
+
 static size_t planes_buf_bytes(const drt3d_plan* P) {
     return align_up(P->planes.buf_elems * 4, 256);
 }
@@ -338,8 +357,8 @@ drt3d_status drt3d_workspace_bytes(const drt3d_plan* P, int op, size_t* bytes) {
         *bytes = 2 * inverse_buf_bytes(P->N);
         return DRT3D_OK;
     case DRT3D_OP_LINES_FORWARD:
-        *bytes = 0;
-        return DRT3D_ERR_INVALID_ARG;  // not built yet
+        *bytes = (size_t)kMaxSlots * djt_buf_bytes(P->N);
+        return DRT3D_OK;
     }
     return DRT3D_ERR_INVALID_ARG;
 }
@@ -511,9 +530,62 @@ drt3d_status drt3d_planes_inverse(const drt3d_plan* P, const int32_t* d_R, int d
 
 drt3d_status djt3d_lines_forward(const drt3d_plan* P, const void* d_in, int32_t* d_out, uint32_t mask,
                                  void* d_ws, size_t ws_bytes, cudaStream_t stream) {
-    (void)d_ws; (void)ws_bytes; (void)stream; (void)mask;
     if (!P || !d_in || !d_out) return DRT3D_ERR_INVALID_ARG;
-    return DRT3D_ERR_INVALID_ARG;  // not built yet
+    if (mask == 0 || (mask & ~DRT3D_ALL_SECTORS)) return DRT3D_ERR_INVALID_ARG;
+    if (P->dtype == DRT3D_F32) return DRT3D_ERR_DTYPE;
+    if (P->N > 256) return DRT3D_ERR_SIZE;
+    if (!aligned16(d_in) || !aligned16(d_out) || !aligned16(d_ws)) return DRT3D_ERR_ALIGN;
+    const int N = P->N, n = P->n;
+    int G[2];
+    const int npass = djt_groups(N, G);
+    const size_t buf = djt_buf_bytes(N);
+    const int nslots = popcount12(mask);
+    if (npass > 1 && (!d_ws || ws_bytes < (size_t)nslots * buf)) return DRT3D_ERR_WORKSPACE;
+    const long long out_block = 4LL * N * N * N * N;  // elements per sector
+    DjtLaunch L{};
+    L.N = N;
+    L.n = n;
+    int m0 = 0;
+    for (int p = 0; p < npass; ++p) {
+        const bool ingest = p == 0, final_ = p == npass - 1;
+        const int m1 = m0 + G[p];
+        int i = 0;
+        for (int k = 0; k < 12; ++k) {
+            if (!((mask >> k) & 1)) continue;
+            DjtSlot& sl = L.slot[i];
+            sl.map = sector_affine(N, k);
+            char* b = static_cast<char*>(d_ws) + (size_t)i * buf;
+            sl.in = ingest ? d_in : (const void*)b;
+            sl.out = final_ ? (void*)(d_out + (size_t)i * out_block) : (void*)b;
+            ++i;
+        }
+        L.m0 = m0;
+        L.in_base = ingest ? N : djt_base(N, m0);
+        L.in_pitch = 2 * N - L.in_base;
+        L.in_plane = (long long)L.in_pitch * L.in_pitch;
+        L.out_base = final_ ? 0 : djt_base(N, m1);
+        L.out_pitch = 2 * N - L.out_base;
+        L.out_plane = (long long)L.out_pitch * L.out_pitch;
+        L.D1 = 2 * N - L.out_base;
+        const int width = 2 * N - L.out_base;
+        const int K = djt_lanes_k(G[p], width);
+        L.V = (32 * K - ((1 << G[p]) - 1)) & ~3;
+        L.ntiles = (32 * K >= width) ? 1 : 1 + (width - 32 * K + L.V - 1) / L.V;
+        L.warps = (1LL << (2 * m0 + (n - m1))) * (1LL << G[p]) * L.D1 * L.ntiles;
+        char nm[40];
+        std::snprintf(nm, sizeof nm, "djt_pass G=%d m0=%d", G[p], m0);
+        const double item = P->dtype == DRT3D_U8 ? 1 : P->dtype == DRT3D_I16 ? 2 : 4;
+        const double in_b = ingest ? (double)N * N * N * item
+                                   : (double)(1LL << (n + m0)) * (N + (1 << m0) - 1.0) * (N + (1 << m0) - 1.0) * 4;
+        const double out_b = final_ ? (double)out_block * 4
+                                    : (double)(1LL << (n + m1)) * (N + (1 << m1) - 1.0) * (N + (1 << m1) - 1.0) * 4;
+        prof_begin(P, stream, nm, nslots * (in_b + out_b));
+        if (launch_djt_pass(L, G[p], K, P->dtype, ingest, final_, nslots, stream) != cudaSuccess)
+            return DRT3D_ERR_CUDA;
+        prof_end(P, stream);
+        m0 = m1;
+    }
+    return DRT3D_OK;
 }
 
 drt3d_status drt3d_set_profiling(drt3d_plan* P, int enable) {

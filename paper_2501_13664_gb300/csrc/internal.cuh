@@ -168,6 +168,27 @@ struct InvLaunch {
 size_t inverse_smem_bytes(int N, int G, int base);
 cudaError_t launch_planes_inverse_pass(const InvLaunch& L, int G, cudaStream_t s);
 
+// One pass of the lines transform (djt.cu).
+struct DjtSlot {
+    const void* in;
+    void* out;
+    Affine map;  // sector frame (first pass)
+};
+struct DjtLaunch {
+    DjtSlot slot[kMaxSlots];
+    int N, n, m0;
+    int in_base, in_pitch;   // input plane window [in_base, 2N)^2
+    long long in_plane;      // elements per input plane
+    int out_base, out_pitch; // output plane window (final: 0, 2N)
+    long long out_plane;
+    int D1;                  // output rows d1 per plane (2N - out_base)
+    int V, ntiles;           // d2 tiling: valid displacements of a non-last tile
+    long long warps;         // warps per slot
+};
+int djt_lanes_k(int G, int width);
+cudaError_t launch_djt_pass(const DjtLaunch& L, int G, int K, drt3d_dtype in_dtype, bool ingest, bool final_,
+                            int nslots, cudaStream_t s);
+
 int fused_valid(int G);  // valid displacements per CTA tile of a G-stage fused pass
 cudaError_t launch_planes_fused(const FusedLaunch& L, int G, ElemKind in_kind, ElemKind out_kind,
                                 bool ingest, int nslots, cudaStream_t s);

@@ -35,7 +35,10 @@ __device__ __forceinline__ float shfl_up(float v, int d) {
     return __shfl_up_sync(0xffffffffu, v, d);
 }
 
-template <int G, int K, int J, typename T>
+// ZB ("zero beyond"): values pulled from past the last lane read as zero
+// instead of stale, so a tile whose input is zero past its end is valid in
+// every position.
+template <int G, int K, int J, bool ZB = false, typename T>
 __device__ __forceinline__ void fwd_stage(T (&v)[1 << G][K]) {
     constexpr int R = 1 << G;
     constexpr int HALF = 1 << J;
@@ -52,7 +55,10 @@ __device__ __forceinline__ void fwd_stage(T (&v)[1 << G][K]) {
             for (int i = 0; i < K; ++i) ext[i] = v[b][i];
 #pragma unroll
             for (int e = 0; e < HALF; ++e)
-                if (e <= tau) ext[K + e] = shfl_down(v[b][e % K], 1 + e / K);
+                if (e <= tau) {
+                    ext[K + e] = shfl_down(v[b][e % K], 1 + e / K);
+                    if (ZB && (int)(threadIdx.x & 31) + 1 + e / K >= 32) ext[K + e] = T(0);
+                }
 #pragma unroll
             for (int lsb = 0; lsb < 2; ++lsb)
 #pragma unroll
@@ -66,11 +72,11 @@ __device__ __forceinline__ void fwd_stage(T (&v)[1 << G][K]) {
         for (int i = 0; i < K; ++i) v[r][i] = nv[r][i];
 }
 
-template <int G, int K, int J = 0, typename T>
+template <int G, int K, int J = 0, bool ZB = false, typename T>
 __device__ __forceinline__ void fwd_all(T (&v)[1 << G][K]) {
     if constexpr (J < G) {
-        fwd_stage<G, K, J>(v);
-        fwd_all<G, K, J + 1>(v);
+        fwd_stage<G, K, J, ZB>(v);
+        fwd_all<G, K, J + 1, ZB>(v);
     }
 }
 
