@@ -1,0 +1,124 @@
+"""The FP32 differentiable planes path: forward + hand-written adjoint behind
+torch.autograd.Function, checked against the FP64 oracle transpose, finite
+differences, the per-cell error bound and a gradient-descent least-squares fit
+(8 x 128^3 float32 volumes, standard normal)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def drt():
+    import paper_2501_13664_gb300 as drt3d
+
+    return drt3d
+
+
+def _dot(a, b):
+    return float(torch.dot(a.flatten().double(), b.flatten().double()))
+
+
+def test_dot_product_against_oracle_transpose(drt, oracle_mod):
+    """<A v, r> on the GPU vs <v, A^T r> with the oracle's FP64 backprojection."""
+    N = 128
+    v = synth.random_float((N, N, N), 500)
+    r = synth.random_float((12, N, N, 3 * N), 501)
+    Av = drt.planes_forward(torch.from_numpy(v).cuda())
+    lhs = _dot(Av, torch.from_numpy(r).cuda())
+    Atr = oracle_mod.planes_adjoint(r.astype(np.float64))
+    rhs = float(np.dot(v.astype(np.float64).ravel(), Atr.ravel()))
+    assert abs(lhs - rhs) <= RTOL * abs(rhs)
+    # and the GPU adjoint against the same oracle transpose
+    gpu_Atr = drt.planes_adjoint(torch.from_numpy(r).cuda()).cpu().numpy().astype(np.float64)
+    mag = oracle_mod.planes_adjoint(np.abs(r).astype(np.float64))
+    assert np.all(np.abs(gpu_Atr - Atr) <= RTOL * mag + 1e-30)
+
+
+def test_forward_per_cell_bound_n128(drt, oracle_mod):
+    N = 128
+    x = synth.c5_batch(N=N, batch=1)[0]
+    got = drt.planes_forward(torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
+    ref = oracle_mod.planes_forward(x.astype(np.float64))
+    mag = oracle_mod.planes_forward(np.abs(x).astype(np.float64))
+    err = np.abs(got - ref)
+    assert np.all(err <= RTOL * mag + 1e-30)
+    rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    assert rel < 1e-6
+
+
+def test_autograd_gradient_matches_finite_differences(drt):
+    """L(x) = <A x, r> is linear, so its central difference with eps = 1 is
+    <A v, r> exactly; autograd returns A^T r through the adjoint kernel."""
+    N = 64
+    x = torch.from_numpy(synth.random_float((N, N, N), 510)).cuda().requires_grad_(True)
+    v = torch.from_numpy(synth.random_float((N, N, N), 511)).cuda()
+    r = torch.from_numpy(synth.random_float((12, N, N, 3 * N), 512)).cuda()
+    loss = (drt.planes(x).double() * r.double()).sum()
+    loss.backward()
+    g_dot_v = _dot(x.grad, v)
+    with torch.no_grad():
+        fd = 0.5 * (_dot(drt.planes(x + v), r) - _dot(drt.planes(x - v), r))
+    assert abs(g_dot_v - fd) <= RTOL * abs(fd)
+
+
+def test_autograd_batched_and_subset(drt):
+    N = 16
+    x = torch.from_numpy(synth.random_float((2, N, N, N), 520)).cuda().requires_grad_(True)
+    y = drt.planes(x, [2, 7])
+    assert y.shape == (2, 2, N, N, 3 * N)
+    y.sum().backward()
+    ones = torch.ones((2, N, N, 3 * N), device="cuda")
+    want = drt.planes_adjoint(ones, [2, 7])
+    assert torch.allclose(x.grad[0], want, rtol=1e-6, atol=1e-4)
+    assert torch.allclose(x.grad[1], want, rtol=1e-6, atol=1e-4)
+
+
+def test_lsq_trajectory_against_fp64_oracle(drt, oracle_mod):
+    """50 steps of gradient descent (step 1/L) at N = 32, batch 2, against the
+    same iteration run with the oracle's FP64 forward and backprojection."""
+    from paper_2501_13664_gb300 import lsq
+
+    N, B, steps = 32, 2, 50
+    xs = synth.c5_batch(N=N, batch=B, seed=5)
+    b64 = np.stack([oracle_mod.planes_forward(x.astype(np.float64)) for x in xs])
+    b = torch.from_numpy(b64.astype(np.float32)).cuda()
+    L = lsq.operator_norm_sq(N)
+    _, losses = lsq.fit(b, steps=steps, L=L)
+    x = np.zeros((B, N, N, N))
+    ref = []
+    for _ in range(steps):
+        r = np.stack([oracle_mod.planes_forward(xi) for xi in x]) - b64
+        ref.append(0.5 * float((r ** 2).sum()))
+        g = np.stack([oracle_mod.planes_adjoint(ri) for ri in r])
+        x = x - g / L
+    ref = np.array(ref)
+    got = np.array(losses)
+    assert np.all(np.diff(got) <= 1e-9 * got[0])  # monotone descent
+    assert np.max(np.abs(got - ref) / ref) < 1e-4
+    assert got[-1] < got[0]
+
+
+def test_config_c5_lsq_fit(drt, oracle_mod):
+    """8 x 128^3 float32 N(0,1) volumes; target b = A x* from the FP64 oracle;
+    50 steps from x = 0 with step 1/L (L from 20 power iterations of A^T A)."""
+    from paper_2501_13664_gb300 import lsq
+
+    N, B = 128, 8
+    xs = synth.c5_batch(N=N, batch=B)
+    b = torch.stack([torch.from_numpy(oracle_mod.planes_forward(x.astype(np.float64)).astype(np.float32))
+                     for x in xs]).cuda()
+    L = lsq.operator_norm_sq(N)
+    assert L > 0
+    x, losses = lsq.fit(b, steps=50, L=L)
+    got = np.array(losses)
+    assert np.all(np.diff(got) <= 1e-7 * got[0])
+    assert got[-1] < got[0]
+    # the fitted volumes move toward x*: residual ||x - x*|| decreases
+    xt = torch.from_numpy(xs).cuda()
+    assert float((x - xt).norm()) < float(xt.norm())
