@@ -161,6 +161,54 @@ drt3d_status djt3d_lines_forward(const drt3d_plan* plan, const void* d_in, int32
                                  uint32_t sector_mask, void* d_ws, size_t ws_bytes,
                                  cudaStream_t stream);
 
+/* Stage-fusion schedule of the planes forward: the n = log2 N stages of
+ * eq.(map3D) run in `ngroups` passes of G[0], G[1], ... stages on both axes
+ * (each 1..4, summing to n).  The default is ceil(n/4) near-equal groups;
+ * an autotuner may set another split.  Changing it changes the forward's
+ * workspace size (query drt3d_workspace_bytes again), never its results.
+ * Errors: INVALID_ARG (bad split). */
+drt3d_status drt3d_plan_set_schedule(drt3d_plan* plan, int ngroups, const int* G);
+drt3d_status drt3d_plan_get_schedule(const drt3d_plan* plan, int* ngroups, int G[8]);
+
+/* ---------------------------------------------------------------------
+ * Batched planes forward: many uint8 volumes of sizes N in {16,...,256} in
+ * one persistent kernel launch (not in the paper, which transforms one cube).
+ * Work items are the CTAs of every pass of every volume and dodecant; a
+ * second-pass item waits for its (volume, dodecant)'s first pass through a
+ * device counter, with a bounded wait (default 2 s) after which the launch
+ * records DRT3D_ERR_TIMEOUT and skips the remaining dependent work.
+ *   1. drt3d_batch_plan_create(&bp, count, Ns, DRT3D_U8, 0)
+ *   2. optionally drt3d_batch_set_schedule(bp, N, ngroups, G) per size
+ *   3. drt3d_batch_workspace_bytes(bp, &bytes); allocate it
+ *   4. drt3d_batch_bind(bp, descs, d_ws, bytes): uploads the work tables
+ *      (allocates small device tables; not for capture)
+ *   5. drt3d_planes_forward_batched(bp, stream): one cudaMemsetAsync and one
+ *      kernel launch, no host synchronisation -- capturable in a CUDA graph
+ *   6. drt3d_batch_get_device_error(bp, stream)
+ * Outputs: descs[i].d_out holds all 12 dodecants of volume i in the layout
+ * of drt3d_planes_forward, bit-identical to it.
+ * --------------------------------------------------------------------- */
+typedef struct drt3d_vol_desc {
+    const void* d_in;  /* N^3 uint8 volume */
+    int32_t* d_out;    /* 12 * N * N * 3N int32 */
+} drt3d_vol_desc;
+
+typedef struct drt3d_batch_plan drt3d_batch_plan;
+
+drt3d_status drt3d_batch_plan_create(drt3d_batch_plan** plan, int count, const int* Ns, drt3d_dtype dtype,
+                                     unsigned flags);
+drt3d_status drt3d_batch_plan_destroy(drt3d_batch_plan* plan);
+drt3d_status drt3d_batch_set_schedule(drt3d_batch_plan* plan, int N, int ngroups, const int* G);
+drt3d_status drt3d_batch_workspace_bytes(const drt3d_batch_plan* plan, size_t* bytes);
+drt3d_status drt3d_batch_bind(drt3d_batch_plan* plan, const drt3d_vol_desc* descs, void* d_ws, size_t ws_bytes);
+drt3d_status drt3d_planes_forward_batched(const drt3d_batch_plan* plan, cudaStream_t stream);
+drt3d_status drt3d_batch_get_device_error(const drt3d_batch_plan* plan, cudaStream_t stream);
+/* Test and tuning hook: bounded-wait limit in nanoseconds; (withhold_vol,
+ * withhold_dodecant) >= 0 makes that first-pass signal never arrive, so the
+ * dependent waits time out (exercises the error path without a GPU fault). */
+drt3d_status drt3d_batch_set_wait_limit(drt3d_batch_plan* plan, unsigned long long ns, int withhold_vol,
+                                        int withhold_dodecant);
+
 /* Synchronise `stream`, read and clear the plan's device status word.
  * Returns DRT3D_OK if no kernel recorded an error since the last call. */
 drt3d_status drt3d_get_device_error(const drt3d_plan* plan, cudaStream_t stream);

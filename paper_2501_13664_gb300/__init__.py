@@ -92,10 +92,90 @@ class Plan:
         return [(self._lib.drt3d_profiled_launch_name(self.handle, i).decode(), float(ms[i]), float(by[i]))
                 for i in range(n)]
 
+    def set_schedule(self, groups) -> None:
+        """Stage-fusion split of the planes forward (e.g. (4, 4) or (3, 3, 2))."""
+        arr = (ctypes.c_int * len(groups))(*[int(g) for g in groups])
+        _abi.check(self._lib.drt3d_plan_set_schedule(self.handle, len(groups), arr), "drt3d_plan_set_schedule")
+
+    def schedule(self) -> tuple:
+        ng = ctypes.c_int()
+        arr = (ctypes.c_int * 8)()
+        _abi.check(self._lib.drt3d_plan_get_schedule(self.handle, ctypes.byref(ng), arr), "drt3d_plan_get_schedule")
+        return tuple(arr[i] for i in range(ng.value))
+
     def __del__(self):
         try:
             if getattr(self, "handle", None):
                 self._lib.drt3d_plan_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+class _VolDesc(ctypes.Structure):
+    _fields_ = [("d_in", ctypes.c_void_p), ("d_out", ctypes.c_void_p)]
+
+
+class BatchPlan:
+    """Planes forward of many uint8 volumes (N in 16..256) in one persistent launch.
+
+    ``bind`` fixes the device buffers; ``run`` enqueues one memset and one
+    kernel on the current stream (capturable in a CUDA graph).
+    """
+
+    def __init__(self, Ns, dtype: torch.dtype = torch.uint8, schedules: dict | None = None):
+        if dtype != torch.uint8:
+            raise TypeError("the batched forward takes uint8 volumes")
+        self.Ns = [int(n) for n in Ns]
+        self._lib = _abi.lib()
+        h = ctypes.c_void_p()
+        arr = (ctypes.c_int * len(self.Ns))(*self.Ns)
+        _abi.check(self._lib.drt3d_batch_plan_create(ctypes.byref(h), len(self.Ns), arr, _abi.DTYPES["u8"], 0),
+                   "drt3d_batch_plan_create")
+        self.handle = h
+        for N, groups in (schedules or {}).items():
+            g = (ctypes.c_int * len(groups))(*[int(x) for x in groups])
+            _abi.check(self._lib.drt3d_batch_set_schedule(self.handle, int(N), len(groups), g),
+                       "drt3d_batch_set_schedule")
+        self._keep = None
+
+    def workspace_bytes(self) -> int:
+        v = ctypes.c_size_t()
+        _abi.check(self._lib.drt3d_batch_workspace_bytes(self.handle, ctypes.byref(v)), "drt3d_batch_workspace_bytes")
+        return int(v.value)
+
+    def bind(self, vols, outs=None, workspace: torch.Tensor | None = None):
+        """Bind device volumes (and outputs, allocated if omitted); returns outs."""
+        if len(vols) != len(self.Ns):
+            raise ValueError("one volume per size")
+        if outs is None:
+            outs = [torch.empty((12, N, N, 3 * N), dtype=torch.int32, device=v.device) for v, N in zip(vols, self.Ns)]
+        for v, o, N in zip(vols, outs, self.Ns):
+            if tuple(v.shape) != (N, N, N) or v.dtype != torch.uint8 or not v.is_cuda or not v.is_contiguous():
+                raise ValueError("volumes must be contiguous cuda uint8 N^3 tensors matching the plan")
+            if tuple(o.shape) != (12, N, N, 3 * N) or o.dtype != torch.int32 or not o.is_contiguous():
+                raise ValueError("outputs must be contiguous (12, N, N, 3N) int32 tensors")
+        nb = self.workspace_bytes()
+        ws = workspace if workspace is not None else torch.empty(max(16, nb), dtype=torch.uint8, device=vols[0].device)
+        descs = (_VolDesc * len(vols))(*[_VolDesc(v.data_ptr(), o.data_ptr()) for v, o in zip(vols, outs)])
+        _abi.check(self._lib.drt3d_batch_bind(self.handle, descs, ws.data_ptr(), ws.numel()), "drt3d_batch_bind")
+        self._keep = (list(vols), list(outs), ws)
+        return outs
+
+    def run(self) -> None:
+        _abi.check(self._lib.drt3d_planes_forward_batched(self.handle, _stream()), "drt3d_planes_forward_batched")
+
+    def device_error(self) -> int:
+        return int(self._lib.drt3d_batch_get_device_error(self.handle, _stream()))
+
+    def set_wait_limit(self, ns: int, withhold_vol: int = -1, withhold_dodecant: int = -1) -> None:
+        _abi.check(self._lib.drt3d_batch_set_wait_limit(self.handle, int(ns), int(withhold_vol),
+                                                        int(withhold_dodecant)), "drt3d_batch_set_wait_limit")
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None):
+                self._lib.drt3d_batch_plan_destroy(self.handle)
                 self.handle = None
         except Exception:
             pass

@@ -39,6 +39,16 @@ SIGNATURES = {
     "drt3d_profiled_launch_name": (ctypes.c_char_p, [P, I]),
     "drt3d_version": (I, []),
     "drt3d_planes_forward_noalloc": (I, [P, P, P, U32, P]),
+    "drt3d_plan_set_schedule": (I, [P, I, ctypes.POINTER(I)]),
+    "drt3d_plan_get_schedule": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+    "drt3d_batch_plan_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(I), I, ctypes.c_uint]),
+    "drt3d_batch_plan_destroy": (I, [P]),
+    "drt3d_batch_set_schedule": (I, [P, I, I, ctypes.POINTER(I)]),
+    "drt3d_batch_workspace_bytes": (I, [P, ctypes.POINTER(SZ)]),
+    "drt3d_batch_bind": (I, [P, P, P, SZ]),
+    "drt3d_planes_forward_batched": (I, [P, P]),
+    "drt3d_batch_get_device_error": (I, [P, P]),
+    "drt3d_batch_set_wait_limit": (I, [P, ctypes.c_ulonglong, I, I]),
     "drt3d_noalloc_scratch_bytes": (SZ, []),
 }
 

@@ -1,0 +1,105 @@
+"""Autotuner for the planes forward's stage-fusion schedule.
+
+For each size N the candidates are the ordered splits of the n = log2 N
+stages into passes of 2..4 stages (each pass applies its stages on both
+axes).  Each candidate is timed with CUDA events on a seeded uint8 volume
+(all 12 dodecants, median of a few launches after warm-up) and the fastest
+is kept.  Results are cached as JSON keyed by device name, SM count, N and
+dtype, at $DRT3D_TUNE_CACHE or ~/.cache/drt3d/tune.json.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import os
+
+import torch
+
+from . import ALL, get_plan, planes_forward
+
+
+def splits(n: int, lo: int = 2, hi: int = 4) -> list:
+    """Ordered compositions of n into parts in [lo, hi] (n < lo: the single part n)."""
+    if n < lo:
+        return [(n,)]
+    out = []
+    for k in range(1, n // lo + 1):
+        for parts in itertools.product(range(lo, hi + 1), repeat=k):
+            if sum(parts) == n:
+                out.append(tuple(parts))
+    return out
+
+
+def _cache_path() -> str:
+    return os.environ.get("DRT3D_TUNE_CACHE", os.path.expanduser("~/.cache/drt3d/tune.json"))
+
+
+def _key(N: int, dtype: torch.dtype) -> str:
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return f"{p.name}|{p.multi_processor_count}|{N}|{str(dtype).replace('torch.', '')}"
+
+
+def load_cache() -> dict:
+    try:
+        with open(_cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(d: dict) -> None:
+    path = _cache_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(d, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+
+
+def time_schedule(vol: torch.Tensor, groups, reps: int = 5) -> float:
+    """Median milliseconds of the 12-dodecant forward under ``groups``."""
+    N = int(vol.shape[0])
+    plan = get_plan(N, vol.dtype)
+    old = plan.schedule()
+    plan.set_schedule(groups)
+    try:
+        out = torch.empty((12, N, N, 3 * N), dtype=torch.int32, device=vol.device)
+        ws = plan.workspace("planes_forward")
+        for _ in range(2):
+            planes_forward(vol, ALL, out=out, workspace=ws)
+        times = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            planes_forward(vol, ALL, out=out, workspace=ws)
+            b.record()
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        times.sort()
+        return times[len(times) // 2]
+    finally:
+        plan.set_schedule(old)
+
+
+def tune(Ns, dtype: torch.dtype = torch.uint8, use_cache: bool = True, seed: int = 11) -> dict:
+    """{N: best split} for the given sizes (and record the timings)."""
+    cache = load_cache() if use_cache else {}
+    best = {}
+    for N in sorted(set(int(n) for n in Ns)):
+        key = _key(N, dtype)
+        if key in cache:
+            best[N] = tuple(cache[key]["groups"])
+            continue
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        vol = torch.randint(0, 256, (N, N, N), generator=g, dtype=torch.int32).to(dtype).cuda()
+        n = N.bit_length() - 1
+        results = {str(s): time_schedule(vol, s) for s in splits(n)}
+        pick = min(results, key=results.get)
+        best[N] = tuple(int(x) for x in pick.strip("()").split(",") if x.strip())
+        cache[key] = {"groups": list(best[N]), "ms": results}
+    if use_cache:
+        save_cache(cache)
+    return best

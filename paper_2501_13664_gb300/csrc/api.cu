@@ -100,15 +100,15 @@ static ElemKind kind_of(drt3d_dtype d) {
     }
 }
 
-FusedSchedule make_fused_schedule(int N, drt3d_dtype dtype) {
+bool make_fused_schedule_groups(int N, drt3d_dtype dtype, int ng, const int* G, FusedSchedule* out) {
     FusedSchedule S{};
-    const int n = ilog2(N);
-    const int ng = (n + 3) / 4;
+    if (ng < 1 || ng > 8) return false;
     int m = 0;
     size_t maxb = 0;
     for (int g = 0; g < ng; ++g) {
+        if (G[g] < 1 || G[g] > 4) return false;
         FusedPass& P = S.pass[g];
-        P.G = n / ng + (g < n % ng ? 1 : 0);
+        P.G = G[g];
         P.m0 = m;
         P.ingest = (g == 0);
         P.in = (g == 0) ? Geo{0, 0} : S.pass[g - 1].out;
@@ -128,13 +128,26 @@ FusedSchedule make_fused_schedule(int N, drt3d_dtype dtype) {
             if (b > maxb) maxb = b;
         }
     }
+    if ((1 << m) != N) return false;
     S.npass = ng;
     S.buf_bytes = maxb;
+    *out = S;
+    return true;
+}
+
+// Default split: ceil(n / 4) groups of near-equal size, larger ones first.
+FusedSchedule make_fused_schedule(int N, drt3d_dtype dtype) {
+    const int n = ilog2(N);
+    const int ng = (n + 3) / 4;
+    int G[8];
+    for (int g = 0; g < ng; ++g) G[g] = n / ng + (g < n % ng ? 1 : 0);
+    FusedSchedule S{};
+    make_fused_schedule_groups(N, dtype, ng, G, &S);
     return S;
 }
 
 // Ingest mode of dodecant k's first pass (see planes_fused.cu).
-static void ingest_mode(int N, const Affine& A, FusedSlot& fs) {
+void fused_ingest_mode(int N, const Affine& A, FusedSlot& fs) {
     fs.swap = 0;
     fs.reverse = 0;
     fs.mode = kIngestGeneric;
@@ -388,7 +401,7 @@ drt3d_status drt3d_planes_forward(const drt3d_plan* P, const void* d_in, void* d
             char* bufB = bufA + buf;
             FusedSlot& fs = L.slot[i];
             fs.map = dodecant_affine(N, k);
-            ingest_mode(N, fs.map, fs);
+            fused_ingest_mode(N, fs.map, fs);
             fs.in = (p == 0) ? d_in : ((p & 1) ? (const void*)bufA : (const void*)bufB);
             fs.out = ps.final_ ? (void*)(static_cast<char*>(d_out) + (size_t)i * out_block)
                                : ((p & 1) ? (void*)bufB : (void*)bufA);
@@ -585,6 +598,21 @@ drt3d_status djt3d_lines_forward(const drt3d_plan* P, const void* d_in, int32_t*
         prof_end(P, stream);
         m0 = m1;
     }
+    return DRT3D_OK;
+}
+
+drt3d_status drt3d_plan_set_schedule(drt3d_plan* P, int ngroups, const int* G) {
+    if (!P || !G) return DRT3D_ERR_INVALID_ARG;
+    FusedSchedule S{};
+    if (!make_fused_schedule_groups(P->N, P->dtype, ngroups, G, &S)) return DRT3D_ERR_INVALID_ARG;
+    P->fused = S;
+    return DRT3D_OK;
+}
+
+drt3d_status drt3d_plan_get_schedule(const drt3d_plan* P, int* ngroups, int G[8]) {
+    if (!P || !ngroups || !G) return DRT3D_ERR_INVALID_ARG;
+    *ngroups = P->fused.npass;
+    for (int g = 0; g < P->fused.npass; ++g) G[g] = P->fused.pass[g].G;
     return DRT3D_OK;
 }
 

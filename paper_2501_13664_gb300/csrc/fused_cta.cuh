@@ -1,0 +1,357 @@
+// fused_cta.cuh -- the CTA body of a fused planes pass (G stages of
+// eq.(map3D) on both axes), shared by the per-pass kernel (planes_fused.cu)
+// and the batched persistent kernel (planes_batched.cu).  See
+// planes_fused.cu for the algorithm.
+#pragma once
+
+#include <type_traits>
+
+#include "internal.cuh"
+#include "warp_drt.cuh"
+
+namespace drt3d {
+namespace fused {
+
+constexpr int K = 4;       // displacements per lane
+constexpr int WT = 32 * K; // displacements per warp tile
+
+template <typename TIn, typename T>
+__device__ __forceinline__ T to_acc(TIn x) {
+    if constexpr (std::is_same<T, float>::value) {
+        return (T)x;
+    } else {
+        return (T)(int32_t)x;  // zero/sign extension into the int32 ring
+    }
+}
+
+// Load `n` elements of TIn starting at p (aligned to min(n*sizeof, 16) bytes).
+template <typename TIn, int NE>
+__device__ __forceinline__ void load_run(const TIn* p, TIn (&dst)[NE]) {
+    constexpr int BYTES = NE * (int)sizeof(TIn);
+    if constexpr (BYTES >= 16) {
+        const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+        for (int c = 0; c < BYTES / 16; ++c) {
+            uint4 w = __ldg(q + c);
+            memcpy(reinterpret_cast<char*>(dst) + 16 * c, &w, 16);
+        }
+    } else if constexpr (BYTES == 8) {
+        uint2 w = __ldg(reinterpret_cast<const uint2*>(p));
+        memcpy(dst, &w, 8);
+    } else if constexpr (BYTES == 4) {
+        unsigned w = __ldg(reinterpret_cast<const unsigned*>(p));
+        memcpy(dst, &w, 4);
+    } else if constexpr (BYTES == 2) {
+        unsigned short w = __ldg(reinterpret_cast<const unsigned short*>(p));
+        memcpy(dst, &w, 2);
+    } else {
+#pragma unroll
+        for (int e = 0; e < NE; ++e) dst[e] = p[e];
+    }
+}
+
+// Number of warps of the fused CTA for a G-stage group: one warp per row
+// group up to 8; with G = 4 each warp handles two groups per phase, so two
+// CTAs (2 x 256 threads, <= 128 registers each) fit on one SM.
+template <int G> __host__ __device__ constexpr int fused_warps() { return G >= 3 ? 8 : (1 << G); }
+// Displacements of a phase-1 result row that phase 2 consumes: V valid
+// outputs plus the 2^G - 1 the phase-2 shifts reach past them.
+template <int G> __host__ __device__ constexpr int fused_v() { return (WT - 2 * ((1 << G) - 1)) & ~3; }
+template <int G> __host__ __device__ constexpr int fused_ws() { return (fused_v<G>() + (1 << G) - 1 + 3) & ~3; }
+
+// Buffer rows are stored on [base, base + pitch) with base and pitch
+// multiples of 8 and hold zeros outside [base, dmax) (dmax a multiple of 4).
+// A lane's window [q, q + K) is covered by the two aligned 4-element chunks
+// starting at q & ~3; each chunk is entirely inside or entirely outside the
+// valid range, so it is one predicated vector load.  r = q & 3 is the same
+// for all lanes of a row.  Loads are issued for all rows first, then the
+// windows are extracted branch-free.
+struct Chunks16 { uint2 c[2]; };   // 8 x 16-bit
+struct Chunks32 { uint4 c[2]; };   // 8 x 32-bit
+
+template <typename TIn>
+using ChunksOf = typename std::conditional<sizeof(TIn) == 2, Chunks16, Chunks32>::type;
+
+template <typename V, bool COHERENT>
+__device__ __forceinline__ V ld_vec(const V* p) {
+    if constexpr (COHERENT) return *p;
+    else return __ldg(p);
+}
+
+template <typename TIn, bool COHERENT>
+__device__ __forceinline__ ChunksOf<TIn> load_chunks(const TIn* row, int base, int dmax, int q) {
+    ChunksOf<TIn> w;
+    const int qa = q & ~3;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const int dc = qa + 4 * c;
+        const bool in = dc >= base && dc < dmax;
+        const TIn* p = row + (in ? dc - base : 0);
+        if constexpr (sizeof(TIn) == 2) {
+            const uint2 x = ld_vec<uint2, COHERENT>(reinterpret_cast<const uint2*>(p));
+            w.c[c] = in ? x : make_uint2(0, 0);
+        } else {
+            const uint4 x = ld_vec<uint4, COHERENT>(reinterpret_cast<const uint4*>(p));
+            w.c[c] = in ? x : make_uint4(0, 0, 0, 0);
+        }
+    }
+    return w;
+}
+
+// Elements r .. r+3 of the 8 loaded ones, as accumulator values.
+template <typename TIn, typename T>
+__device__ __forceinline__ void extract4(const ChunksOf<TIn>& w, int r, T (&v)[K]) {
+    if constexpr (sizeof(TIn) == 2) {
+        const uint32_t x0 = w.c[0].x, x1 = w.c[0].y, x2 = w.c[1].x, x3 = w.c[1].y;
+        const bool hi = (r & 2) != 0;
+        const uint32_t a0 = hi ? x1 : x0, a1 = hi ? x2 : x1, a2 = hi ? x3 : x2;
+        const uint32_t sh = (uint32_t)(r & 1) * 16u;
+        const uint32_t o0 = __funnelshift_r(a0, a1, sh);
+        const uint32_t o1 = __funnelshift_r(a1, a2, sh);
+        const uint32_t e[4] = {o0 & 0xFFFFu, o0 >> 16, o1 & 0xFFFFu, o1 >> 16};
+#pragma unroll
+        for (int i = 0; i < K; ++i) v[i] = to_acc<TIn, T>((TIn)e[i]);
+    } else {
+        const uint32_t x[8] = {w.c[0].x, w.c[0].y, w.c[0].z, w.c[0].w, w.c[1].x, w.c[1].y, w.c[1].z, w.c[1].w};
+        uint32_t t[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) t[j] = (r & 2) ? x[j + 2] : x[j];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            const uint32_t bits = (r & 1) ? t[i + 1] : t[i];
+            TIn e;
+            memcpy(&e, &bits, 4);
+            v[i] = to_acc<TIn, T>(e);
+        }
+    }
+}
+
+// Phase-2 store of output rows (t1, t2), t2 < 2^G, over the tile's first V
+// displacements: aligned vector stores where a lane's K values are all valid.
+template <typename TOut, typename T, int G>
+__device__ __forceinline__ void store_rows(const FusedLaunch& L, const FusedSlot& sp, const T (&v)[1 << G][K],
+                                           int t1, int sg1, int wq1, int sg2, int wq2, int rs1, int rs2,
+                                           int d0, int lane) {
+    constexpr int R = 1 << G;
+    const int m0 = L.m0;
+    const int o1 = t1 + (sg1 << G) + (wq1 << (m0 + G));
+    TOut* out = static_cast<TOut*>(sp.out);
+    const int p0 = lane * K;
+    const int d = d0 + p0;
+    const bool full = (p0 + K <= L.V) && (d + K <= L.dmax) && L.vec_store;
+    const long long orow0 = (long long)o1 * rs1 + (long long)((sg2 << G) + (wq2 << (m0 + G))) * rs2;
+#pragma unroll
+    for (int t2 = 0; t2 < R; ++t2) {
+        TOut* dst = out + (orow0 + (long long)t2 * rs2) * L.gout.pitch + (d - L.gout.base);
+        if (full) {
+            TOut e[K];
+#pragma unroll
+            for (int i = 0; i < K; ++i) e[i] = (TOut)v[t2][i];
+            if constexpr (sizeof(TOut) == 4) {
+                uint4 w;
+                memcpy(&w, e, 16);
+                *reinterpret_cast<uint4*>(dst) = w;
+            } else {
+                uint2 w;
+                memcpy(&w, e, 8);
+                *reinterpret_cast<uint2*>(dst) = w;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < K; ++i)
+                if (p0 + i < L.V && d + i < L.dmax) dst[i] = (TOut)v[t2][i];
+        }
+    }
+}
+
+// One CTA of a fused pass: unit/tile `cta` of slot `sp`.  All threads of
+// the block must call it (it synchronises); warps at or past fused_warps<G>()
+// idle.  With COHERENT the input is read with plain loads instead of the
+// read-only path (the batched kernel reads buffers other CTAs of the same
+// launch wrote).
+template <typename TIn, typename TOut, typename T, typename TS, int G, bool INGEST, bool COHERENT>
+__device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot& sp, unsigned cta,
+                                          unsigned char* smem_raw) {
+    constexpr int R = 1 << G;
+    constexpr int NW = fused_warps<G>();
+    constexpr int GPW = R / NW > 0 ? R / NW : 1;  // row groups per warp
+    constexpr int WS = fused_ws<G>();
+    TS* S = reinterpret_cast<TS*>(smem_raw);  // [t1][u2][WS] (+ K pad)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool active = warp < NW;
+    const int m0 = L.m0;
+    const int N = L.N;
+    const unsigned ntiles = (unsigned)L.ntiles;
+    unsigned unit = cta / ntiles;
+    const int tile = (int)(cta - unit * ntiles);
+    const int wb = L.n - m0 - G;
+    const int sg1 = (int)(unit & ((1u << m0) - 1)); unit >>= m0;
+    const int wq1 = (int)(unit & ((1u << wb) - 1)); unit >>= wb;
+    const int sg2 = (int)(unit & ((1u << m0) - 1)); unit >>= m0;
+    const int wq2 = (int)unit;
+    const int d0 = L.gout.base + tile * L.V;
+    const bool swap = sp.swap != 0;
+    // Row strides (in rows) of the two axes within the [i1][i2] layout.
+    const int rs1 = swap ? 1 : N, rs2 = swap ? N : 1;
+    // An output row with slopes-so-far (s1, s2) vanishes below d = 2N - s1 - s2
+    // (every digital-line value l^m_s(u) is at most s).  A tile that lies below
+    // that bound for the unit's largest slopes is all zeros: store them and
+    // skip the loads and both transforms.
+    const int smax1 = (sg1 << G) + (1 << G) - 1, smax2 = (sg2 << G) + (1 << G) - 1;
+    const bool zero_tile = d0 + L.V <= 2 * N - smax1 - smax2;
+
+    if (zero_tile) {
+        if (!active) return;
+#pragma unroll 1
+        for (int gi = 0; gi < GPW; ++gi) {
+            const int t1 = warp + gi * NW;
+            T v[R][K];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int i = 0; i < K; ++i) v[r][i] = T(0);
+            store_rows<TOut, T, G>(L, sp, v, t1, sg1, wq1, sg2, wq2, rs1, rs2, d0, lane);
+        }
+        return;
+    }
+
+    // ---------------- phase 1: transform along axis 1, warp = u2 ----------
+#pragma unroll 1
+    for (int gi = 0; gi < (active ? GPW : 0); ++gi) {
+        const int u2 = warp + gi * NW;
+        const int a2 = sg2 + (u2 << m0) + (wq2 << (m0 + G));
+        const int start = d0 + sg2 * u2 + lane * K;
+        T v[R][K];
+        if constexpr (INGEST) {
+            // m0 == 0 here: no shear, rows a1 = u1 + (wq1 << G).
+            const TIn* vol = static_cast<const TIn*>(sp.in);
+            const int z0 = start - 2 * N;
+            const long long sx = swap ? sp.map.sy : sp.map.sx;   // stride of the phase-1 axis
+            const long long s2 = swap ? sp.map.sx : sp.map.sy;   // stride of the phase-2 axis
+            const long long rowbase = sp.map.o0 + (long long)a2 * s2 + (long long)(wq1 << G) * sx;
+            if (sp.mode == kIngestZ) {
+                // K consecutive z' of each row are contiguous (stride +-1).
+                const bool in = z0 >= 0 && z0 < N;
+                const int zc = in ? z0 : 0;  // clamp: always a valid, aligned address
+#pragma unroll
+                for (int u1 = 0; u1 < R; ++u1) {
+                    TIn e[K];
+                    {
+                        const long long b = rowbase + (long long)u1 * sx + (long long)zc * sp.map.sz;
+                        load_run<TIn, K>(vol + (sp.reverse ? b - (K - 1) : b), e);
+                    }
+#pragma unroll
+                    for (int i = 0; i < K; ++i)
+                        v[u1][i] = in ? to_acc<TIn, T>(sp.reverse ? e[K - 1 - i] : e[i]) : T(0);
+                }
+            } else if (sp.mode == kIngestRun) {
+                // The R rows of the block are contiguous at every z'.
+#pragma unroll
+                for (int i = 0; i < K; ++i) {
+                    const int z = z0 + i;
+                    TIn e[R];
+                    const bool in = z >= 0 && z < N;
+                    {
+                        const long long b = rowbase + (long long)(in ? z : 0) * sp.map.sz;
+                        load_run<TIn, R>(vol + (sp.reverse ? b - (R - 1) : b), e);
+                    }
+#pragma unroll
+                    for (int u1 = 0; u1 < R; ++u1)
+                        v[u1][i] = in ? to_acc<TIn, T>(sp.reverse ? e[R - 1 - u1] : e[u1]) : T(0);
+                }
+            } else {
+#pragma unroll
+                for (int u1 = 0; u1 < R; ++u1)
+#pragma unroll
+                    for (int i = 0; i < K; ++i) {
+                        const int z = z0 + i;
+                        v[u1][i] = (z >= 0 && z < N)
+                                       ? to_acc<TIn, T>(vol[rowbase + (long long)u1 * sx + (long long)z * sp.map.sz])
+                                       : T(0);
+                    }
+            }
+        } else {
+            // A group whose sheared windows all miss the stored range [base, dmax)
+            // reads only zeros: park zeros and skip the loads and the transform.
+            const int g_lo = d0 + sg2 * u2, g_hi = g_lo + sg1 * (R - 1) + WT + 4;
+            if (g_hi <= L.gin.base || g_lo >= L.dmax) {
+                if (lane * K < WS) {
+#pragma unroll
+                    for (int t1 = 0; t1 < R; ++t1) {
+                        TS* dst = S + ((t1 * R + u2) * WS + lane * K);
+#pragma unroll
+                        for (int i = 0; i < K; ++i) dst[i] = TS(0);
+                    }
+                }
+                continue;
+            }
+            const TIn* buf = static_cast<const TIn*>(sp.in);
+            const long long row0 = (long long)(sg1 + (wq1 << (m0 + G))) * rs1 + (long long)a2 * rs2;
+            const long long rstep = (long long)rs1 << m0;  // rows between u1 and u1 + 1
+            // Issue the loads of up to 16 x 16-bit or 8 x 32-bit rows, then extract.
+            constexpr int BATCH = sizeof(TIn) == 2 ? R : (R < 8 ? R : 8);
+#pragma unroll
+            for (int b0 = 0; b0 < R; b0 += BATCH) {
+                ChunksOf<TIn> w[BATCH];
+#pragma unroll
+                for (int j = 0; j < BATCH; ++j) {
+                    const int u1 = b0 + j;
+                    const TIn* rowp = buf + (row0 + u1 * rstep) * L.gin.pitch;
+                    w[j] = load_chunks<TIn, COHERENT>(rowp, L.gin.base, L.dmax, start + sg1 * u1);
+                }
+#pragma unroll
+                for (int j = 0; j < BATCH; ++j) {
+                    const int u1 = b0 + j;
+                    extract4<TIn, T>(w[j], (start + sg1 * u1) & 3, v[u1]);
+                }
+            }
+        }
+        fwd_all<G, K>(v);
+        if (lane * K < WS) {
+#pragma unroll
+            for (int t1 = 0; t1 < R; ++t1) {
+                TS* dst = S + ((t1 * R + u2) * WS + lane * K);
+                TS e[K];
+#pragma unroll
+                for (int i = 0; i < K; ++i) e[i] = (TS)v[t1][i];
+                if constexpr (sizeof(TS) == 4) {
+                    uint4 w;
+                    memcpy(&w, e, 16);
+                    *reinterpret_cast<uint4*>(dst) = w;
+                } else {
+                    uint2 w;
+                    memcpy(&w, e, 8);
+                    *reinterpret_cast<uint2*>(dst) = w;
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---------------- phase 2: transform along axis 2, warp = t1 ----------
+#pragma unroll 1
+    for (int gi = 0; gi < (active ? GPW : 0); ++gi) {
+        const int t1 = warp + gi * NW;
+        T v[R][K];
+#pragma unroll
+        for (int u2 = 0; u2 < R; ++u2) {
+            // lanes past WS read the next row (or the pad): values they feed are invalid
+            const TS* src = S + ((t1 * R + u2) * WS + lane * K);
+            TS e[K];
+            if constexpr (sizeof(TS) == 4) {
+                uint4 w = *reinterpret_cast<const uint4*>(src);
+                memcpy(e, &w, 16);
+            } else {
+                uint2 w = *reinterpret_cast<const uint2*>(src);
+                memcpy(e, &w, 8);
+            }
+#pragma unroll
+            for (int i = 0; i < K; ++i) v[u2][i] = (T)e[i];
+        }
+        fwd_all<G, K>(v);
+        store_rows<TOut, T, G>(L, sp, v, t1, sg1, wq1, sg2, wq2, rs1, rs2, d0, lane);
+    }
+}
+
+}  // namespace fused
+}  // namespace drt3d

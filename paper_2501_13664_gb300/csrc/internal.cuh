@@ -150,6 +150,10 @@ struct FusedSchedule {
 };
 
 FusedSchedule make_fused_schedule(int N, drt3d_dtype dtype);
+// Schedule from an explicit split of the n stages into ng groups (each 1..4).
+bool make_fused_schedule_groups(int N, drt3d_dtype dtype, int ng, const int* G, FusedSchedule* out);
+// Ingest mode (vector load pattern, axis order) of one dodecant's first pass.
+void fused_ingest_mode(int N, const Affine& A, FusedSlot& fs);
 
 // Launchers (implemented per .cu file); return cudaGetLastError().
 // One pass of the exact inverse: undo G half-stages along one axis.

@@ -1,0 +1,398 @@
+// planes_batched.cu -- the planes forward transform of many volumes of
+// different sizes in one persistent launch.
+//
+// Work items are the CTAs of every fused pass of every volume and dodecant
+// (see planes_fused.cu).  They are numbered pass-major: all first-pass items
+// of all volumes, then all second-pass items, ...; within a (pass, volume)
+// segment item i is dodecant slot i / ctas, unit-tile i % ctas.  Resident
+// CTAs (two per SM) take items from an atomic counter.  An item of pass p > 0
+// reads the intermediate written by every pass p-1 item of its (volume,
+// dodecant); those items were all handed out before it, to CTAs that are
+// running, so the item waits for their completion counter -- a bounded wait:
+// after the time limit it records DRT3D_ERR_TIMEOUT in the status word, sets
+// an abort flag that ends all other waits, and skips its work.
+//
+// One call is one memset of the counters and one kernel launch on the
+// caller's stream, so it can be captured in a CUDA graph.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fused_cta.cuh"
+
+namespace drt3d {
+
+constexpr int kBatchMaxPass = 4;
+
+struct BatchVol {
+    FusedLaunch pass[kBatchMaxPass];
+    int npass;
+    int G[kBatchMaxPass];
+    int in_kind[kBatchMaxPass], out_kind[kBatchMaxPass];
+    unsigned ctas[kBatchMaxPass];  // items per dodecant slot
+};
+
+struct BatchArgs {
+    const BatchVol* vols;
+    const unsigned* seg_start;  // nseg + 1 entries
+    const int* seg_vol;
+    const int* seg_pass;
+    int nseg;
+    unsigned nitems;
+    unsigned* next;     // work counter
+    unsigned* abort;    // set once a wait gives up
+    unsigned* done;     // [vol][12][kBatchMaxPass] completed items
+    int* status;
+    unsigned long long wait_ns;
+    int withhold_vol, withhold_slot;  // test hook: this (vol, slot) never signals pass 0
+};
+
+namespace {
+
+using namespace fused;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Thread 0 only: wait until *ctr >= target.  Returns false when it gives up.
+__device__ bool wait_counter(const BatchArgs& A, const unsigned* ctr, unsigned target) {
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (*(volatile const unsigned*)ctr >= target) {
+            __threadfence();
+            return true;
+        }
+        if (*(volatile const unsigned*)A.abort) return false;
+        if (global_ns() - t0 > A.wait_ns) {
+            atomicCAS(A.status, 0, (int)DRT3D_ERR_TIMEOUT);
+            atomicExch(A.abort, 1u);
+            return false;
+        }
+        __nanosleep(256);
+    }
+}
+
+template <typename TIn, typename TOut, typename TS, int G, bool INGEST>
+__device__ __forceinline__ void run_g(const FusedLaunch& L, int slot, unsigned cta, unsigned char* smem) {
+    fused_cta<TIn, TOut, uint32_t, TS, G, INGEST, true>(L, L.slot[slot], cta, smem);
+}
+
+template <typename TIn, typename TOut, typename TS, bool INGEST>
+__device__ __forceinline__ void run_kind(const FusedLaunch& L, int G, int slot, unsigned cta, unsigned char* smem) {
+    switch (G) {
+    case 2: run_g<TIn, TOut, TS, 2, INGEST>(L, slot, cta, smem); break;
+    case 3: run_g<TIn, TOut, TS, 3, INGEST>(L, slot, cta, smem); break;
+    default: run_g<TIn, TOut, TS, 4, INGEST>(L, slot, cta, smem); break;
+    }
+}
+
+__global__ void __launch_bounds__(256, 2) planes_batched(const __grid_constant__ BatchArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned s_item;
+    __shared__ int s_go;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(A.next, 1u);
+        __syncthreads();
+        const unsigned item = s_item;
+        if (item >= A.nitems) return;
+        int lo = 0, hi = A.nseg - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (A.seg_start[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const int v = A.seg_vol[lo], p = A.seg_pass[lo];
+        const BatchVol& B = A.vols[v];
+        const unsigned local = item - A.seg_start[lo];
+        const int slot = (int)(local / B.ctas[p]);
+        const unsigned cta = local % B.ctas[p];
+        unsigned* done = A.done + ((size_t)v * kMaxSlots + slot) * kBatchMaxPass;
+        if (p > 0) {
+            if (threadIdx.x == 0) s_go = wait_counter(A, done + (p - 1), B.ctas[p - 1]) ? 1 : 0;
+            __syncthreads();
+            if (!s_go) continue;
+        }
+        const FusedLaunch& L = B.pass[p];
+        const int G = B.G[p];
+        const int ik = B.in_kind[p], ok = B.out_kind[p];
+        if (p == 0) {
+            if (ok == (int)ElemKind::U16) run_kind<uint8_t, uint16_t, uint16_t, true>(L, G, slot, cta, smem);
+            else run_kind<uint8_t, uint32_t, uint16_t, true>(L, G, slot, cta, smem);
+        } else if (ik == (int)ElemKind::U16) {
+            if (ok == (int)ElemKind::U16) run_kind<uint16_t, uint16_t, uint32_t, false>(L, G, slot, cta, smem);
+            else run_kind<uint16_t, uint32_t, uint32_t, false>(L, G, slot, cta, smem);
+        } else {
+            run_kind<uint32_t, uint32_t, uint32_t, false>(L, G, slot, cta, smem);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && !(p == 0 && v == A.withhold_vol && slot == A.withhold_slot)) {
+            __threadfence();
+            atomicAdd(done + p, 1u);
+        }
+    }
+}
+
+size_t batched_smem_bytes() { return ((size_t)(1 << 8) * fused_ws<4>() + K) * sizeof(uint32_t); }
+
+}  // namespace
+
+// Opt the kernel into its shared-memory size once per device (done at bind,
+// so a launch inside stream capture issues only stream work).
+cudaError_t batched_prepare(int device) {
+    static unsigned long long done = 0;
+    if (device < 64 && ((done >> device) & 1ull)) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(planes_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)batched_smem_bytes());
+    if (e == cudaSuccess && device < 64) done |= 1ull << device;
+    return e;
+}
+
+cudaError_t launch_planes_batched(const BatchArgs& A, int grid, cudaStream_t s) {
+    planes_batched<<<grid, 256, batched_smem_bytes(), s>>>(A);
+    return cudaGetLastError();
+}
+
+int batched_grid(int device) {
+    if (batched_prepare(device) != cudaSuccess) return 0;
+    int sms = 0, per = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, planes_batched, 256, batched_smem_bytes()) != cudaSuccess)
+        return 0;
+    return sms * std::max(per, 1);
+}
+
+}  // namespace drt3d
+
+using namespace drt3d;
+
+struct drt3d_batch_plan {
+    int count = 0;
+    std::vector<int> Ns;
+    drt3d_dtype dtype = DRT3D_U8;
+    int device = 0;
+    int* d_status = nullptr;
+    std::vector<FusedSchedule> sched;  // per volume
+    // bound state
+    bool bound = false;
+    BatchVol* d_vols = nullptr;
+    unsigned* d_seg_start = nullptr;
+    int* d_seg_vol = nullptr;
+    int* d_seg_pass = nullptr;
+    unsigned* d_counters = nullptr;  // next, abort, done[count][12][kBatchMaxPass]
+    size_t counters_bytes = 0;
+    int nseg = 0;
+    unsigned nitems = 0;
+    int grid = 0;
+    unsigned long long wait_ns = 2000000000ull;
+    int withhold_vol = -1, withhold_slot = -1;
+};
+
+namespace {
+
+void free_bound(drt3d_batch_plan* B) {
+    cudaFree(B->d_vols);
+    cudaFree(B->d_seg_start);
+    cudaFree(B->d_seg_vol);
+    cudaFree(B->d_seg_pass);
+    cudaFree(B->d_counters);
+    B->d_vols = nullptr;
+    B->d_seg_start = nullptr;
+    B->d_seg_vol = nullptr;
+    B->d_seg_pass = nullptr;
+    B->d_counters = nullptr;
+    B->bound = false;
+}
+
+size_t vol_ws_bytes(const FusedSchedule& S) { return S.npass > 1 ? (size_t)kMaxSlots * 2 * S.buf_bytes : 0; }
+
+}  // namespace
+
+extern "C" {
+
+drt3d_status drt3d_batch_plan_create(drt3d_batch_plan** plan, int count, const int* Ns, drt3d_dtype dtype,
+                                     unsigned flags) {
+    if (!plan) return DRT3D_ERR_INVALID_ARG;
+    *plan = nullptr;
+    if (count <= 0 || !Ns || flags != 0) return DRT3D_ERR_INVALID_ARG;
+    if (dtype != DRT3D_U8) return DRT3D_ERR_DTYPE;
+    for (int i = 0; i < count; ++i)
+        if (Ns[i] < 16 || Ns[i] > 256 || (Ns[i] & (Ns[i] - 1))) return DRT3D_ERR_SIZE;
+    drt3d_batch_plan* B = new (std::nothrow) drt3d_batch_plan();
+    if (!B) return DRT3D_ERR_NO_MEMORY;
+    B->count = count;
+    B->Ns.assign(Ns, Ns + count);
+    B->dtype = dtype;
+    if (cudaGetDevice(&B->device) != cudaSuccess) { delete B; return DRT3D_ERR_CUDA; }
+    if (cudaMalloc(&B->d_status, sizeof(int)) != cudaSuccess) { delete B; return DRT3D_ERR_NO_MEMORY; }
+    cudaMemset(B->d_status, 0, sizeof(int));
+    for (int i = 0; i < count; ++i) B->sched.push_back(make_fused_schedule(Ns[i], dtype));
+    *plan = B;
+    return DRT3D_OK;
+}
+
+drt3d_status drt3d_batch_plan_destroy(drt3d_batch_plan* B) {
+    if (!B) return DRT3D_OK;
+    free_bound(B);
+    cudaFree(B->d_status);
+    delete B;
+    return DRT3D_OK;
+}
+
+drt3d_status drt3d_batch_set_schedule(drt3d_batch_plan* B, int N, int ngroups, const int* G) {
+    if (!B || !G) return DRT3D_ERR_INVALID_ARG;
+    if (ngroups < 1 || ngroups > kBatchMaxPass) return DRT3D_ERR_INVALID_ARG;
+    int sum = 0;
+    for (int g = 0; g < ngroups; ++g) {
+        if (G[g] < 2 || G[g] > 4) return DRT3D_ERR_INVALID_ARG;
+        sum += G[g];
+    }
+    if ((1 << sum) != N) return DRT3D_ERR_SIZE;
+    FusedSchedule S;
+    if (!make_fused_schedule_groups(N, B->dtype, ngroups, G, &S)) return DRT3D_ERR_INVALID_ARG;
+    for (int i = 0; i < B->count; ++i)
+        if (B->Ns[i] == N) B->sched[i] = S;
+    if (B->bound) free_bound(B);
+    return DRT3D_OK;
+}
+
+drt3d_status drt3d_batch_workspace_bytes(const drt3d_batch_plan* B, size_t* bytes) {
+    if (!B || !bytes) return DRT3D_ERR_INVALID_ARG;
+    size_t t = 0;
+    for (int i = 0; i < B->count; ++i) t += align_up(vol_ws_bytes(B->sched[i]), 256);
+    *bytes = t;
+    return DRT3D_OK;
+}
+
+drt3d_status drt3d_batch_bind(drt3d_batch_plan* B, const drt3d_vol_desc* descs, void* d_ws, size_t ws_bytes) {
+    if (!B || !descs) return DRT3D_ERR_INVALID_ARG;
+    size_t need = 0;
+    drt3d_batch_workspace_bytes(B, &need);
+    if (need > 0 && (!d_ws || ws_bytes < need)) return DRT3D_ERR_WORKSPACE;
+    for (int i = 0; i < B->count; ++i) {
+        if (!descs[i].d_in || !descs[i].d_out) return DRT3D_ERR_INVALID_ARG;
+        if (((uintptr_t)descs[i].d_in & 15) || ((uintptr_t)descs[i].d_out & 15)) return DRT3D_ERR_ALIGN;
+    }
+    if (((uintptr_t)d_ws & 15)) return DRT3D_ERR_ALIGN;
+    free_bound(B);
+    std::vector<BatchVol> vols(B->count);
+    char* ws = static_cast<char*>(d_ws);
+    int maxpass = 0;
+    for (int v = 0; v < B->count; ++v) {
+        const int N = B->Ns[v];
+        const FusedSchedule& S = B->sched[v];
+        BatchVol& bv = vols[v];
+        std::memset(&bv, 0, sizeof(bv));
+        bv.npass = S.npass;
+        maxpass = std::max(maxpass, S.npass);
+        const size_t buf = S.buf_bytes;
+        const size_t out_block = (size_t)N * N * 3 * N * 4;
+        for (int p = 0; p < S.npass; ++p) {
+            const FusedPass& ps = S.pass[p];
+            FusedLaunch& L = bv.pass[p];
+            L.N = N;
+            L.n = ilog2(N);
+            L.dmax = 3 * N;
+            L.m0 = ps.m0;
+            L.gin = ps.in;
+            L.gout = ps.out;
+            L.V = fused_valid(ps.G);
+            L.ntiles = (3 * N - ps.out.base + L.V - 1) / L.V;
+            const long long per_axis = 1LL << (L.n - ps.G);
+            L.ctas = per_axis * per_axis * L.ntiles;
+            L.vec_store = (ps.out.pitch % 4 == 0) && (ps.out.base % 4 == 0);
+            for (int k = 0; k < 12; ++k) {
+                char* bufA = ws + (size_t)k * 2 * buf;
+                char* bufB = bufA + buf;
+                FusedSlot& fs = L.slot[k];
+                fs.map = dodecant_affine(N, k);
+                fused_ingest_mode(N, fs.map, fs);
+                fs.in = (p == 0) ? descs[v].d_in : ((p & 1) ? (const void*)bufA : (const void*)bufB);
+                fs.out = ps.final_ ? (void*)(reinterpret_cast<char*>(descs[v].d_out) + (size_t)k * out_block)
+                                   : ((p & 1) ? (void*)bufB : (void*)bufA);
+            }
+            bv.G[p] = ps.G;
+            bv.in_kind[p] = (int)ps.in_kind;
+            bv.out_kind[p] = (int)ps.out_kind;
+            bv.ctas[p] = (unsigned)L.ctas;
+        }
+        ws += align_up(vol_ws_bytes(S), 256);
+    }
+    // pass-major segments
+    std::vector<unsigned> seg_start;
+    std::vector<int> seg_vol, seg_pass;
+    unsigned n = 0;
+    for (int p = 0; p < maxpass; ++p)
+        for (int v = 0; v < B->count; ++v) {
+            if (p >= vols[v].npass) continue;
+            seg_start.push_back(n);
+            seg_vol.push_back(v);
+            seg_pass.push_back(p);
+            n += vols[v].ctas[p] * 12u;
+        }
+    seg_start.push_back(n);
+    B->nseg = (int)seg_vol.size();
+    B->nitems = n;
+    B->counters_bytes = (2 + (size_t)B->count * kMaxSlots * kBatchMaxPass) * sizeof(unsigned);
+    bool ok = cudaMalloc(&B->d_vols, vols.size() * sizeof(BatchVol)) == cudaSuccess &&
+              cudaMalloc(&B->d_seg_start, seg_start.size() * sizeof(unsigned)) == cudaSuccess &&
+              cudaMalloc(&B->d_seg_vol, seg_vol.size() * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&B->d_seg_pass, seg_pass.size() * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&B->d_counters, B->counters_bytes) == cudaSuccess;
+    if (!ok) { free_bound(B); return DRT3D_ERR_NO_MEMORY; }
+    ok = cudaMemcpy(B->d_vols, vols.data(), vols.size() * sizeof(BatchVol), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(B->d_seg_start, seg_start.data(), seg_start.size() * sizeof(unsigned),
+                    cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(B->d_seg_vol, seg_vol.data(), seg_vol.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(B->d_seg_pass, seg_pass.data(), seg_pass.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) { free_bound(B); return DRT3D_ERR_CUDA; }
+    B->grid = batched_grid(B->device);
+    if (B->grid <= 0) { free_bound(B); return DRT3D_ERR_CUDA; }
+    B->bound = true;
+    return DRT3D_OK;
+}
+
+drt3d_status drt3d_planes_forward_batched(const drt3d_batch_plan* B, cudaStream_t stream) {
+    if (!B || !B->bound) return DRT3D_ERR_INVALID_ARG;
+    if (cudaMemsetAsync(B->d_counters, 0, B->counters_bytes, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+    BatchArgs A;
+    A.vols = B->d_vols;
+    A.seg_start = B->d_seg_start;
+    A.seg_vol = B->d_seg_vol;
+    A.seg_pass = B->d_seg_pass;
+    A.nseg = B->nseg;
+    A.nitems = B->nitems;
+    A.next = B->d_counters;
+    A.abort = B->d_counters + 1;
+    A.done = B->d_counters + 2;
+    A.status = B->d_status;
+    A.wait_ns = B->wait_ns;
+    A.withhold_vol = B->withhold_vol;
+    A.withhold_slot = B->withhold_slot;
+    if (launch_planes_batched(A, B->grid, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+    return DRT3D_OK;
+}
+
+drt3d_status drt3d_batch_get_device_error(const drt3d_batch_plan* B, cudaStream_t stream) {
+    if (!B) return DRT3D_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+    int h = 0;
+    if (cudaMemcpy(&h, B->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return DRT3D_ERR_CUDA;
+    if (h != 0 && cudaMemset(B->d_status, 0, sizeof(int)) != cudaSuccess) return DRT3D_ERR_CUDA;
+    return (drt3d_status)h;
+}
+
+drt3d_status drt3d_batch_set_wait_limit(drt3d_batch_plan* B, unsigned long long ns, int withhold_vol,
+                                        int withhold_dodecant) {
+    if (!B || ns == 0) return DRT3D_ERR_INVALID_ARG;
+    B->wait_ns = ns;
+    B->withhold_vol = withhold_vol;
+    B->withhold_slot = withhold_dodecant;
+    return DRT3D_OK;
+}
+
+}  // extern "C"

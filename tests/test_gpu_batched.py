@@ -1,0 +1,116 @@
+"""The batched persistent planes forward (many uint8 volumes of uneven N in one
+launch) against one-by-one calls and the oracle; schedules, graph replay and
+the bounded-wait error path."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def drt():
+    import paper_2501_13664_gb300 as drt3d
+
+    return drt3d
+
+
+def _vols(Ns, seed0):
+    return [torch.from_numpy(synth.c2_volume(N, seed=seed0 + i)).cuda() for i, N in enumerate(Ns)]
+
+
+def test_small_mixed_batch_matches_one_by_one_and_oracle(drt, oracle_mod):
+    Ns = [16, 32, 64, 32, 16, 128, 64]
+    vols = _vols(Ns, 40)
+    bp = drt.BatchPlan(Ns)
+    outs = bp.bind(vols)
+    bp.run()
+    assert bp.device_error() == 0
+    for v, o, N in zip(vols, outs, Ns):
+        assert torch.equal(o, drt.planes_forward(v))
+        if N <= 32:
+            np.testing.assert_array_equal(o.cpu().numpy(), oracle_mod.planes_forward(v.cpu().numpy()))
+
+
+def test_schedule_overrides_give_identical_results(drt):
+    Ns = [64, 128, 256, 32]
+    vols = _vols(Ns, 60)
+    ref = [drt.planes_forward(v) for v in vols]
+    bp = drt.BatchPlan(Ns, schedules={64: (2, 2, 2), 128: (2, 3, 2), 256: (3, 3, 2), 32: (2, 3)})
+    outs = bp.bind(vols)
+    bp.run()
+    assert bp.device_error() == 0
+    for o, r in zip(outs, ref):
+        assert torch.equal(o, r)
+    # and the same splits on single-volume plans
+    for v, r, groups in zip(vols, ref, [(2, 2, 2), (3, 2, 2), (2, 2, 2, 2), (3, 2)]):
+        plan = drt.get_plan(int(v.shape[0]), torch.uint8)
+        old = plan.schedule()
+        plan.set_schedule(groups)
+        try:
+            assert torch.equal(drt.planes_forward(v), r)
+        finally:
+            plan.set_schedule(old)
+
+
+def test_config_c4_batch_matches_one_by_one(drt, oracle_mod):
+    """96 volumes, sizes 16:30, 32:30, 64:20, 128:10, 256:6 shuffled."""
+    sizes = synth.c4_sizes()
+    vols = [torch.from_numpy(v).cuda() for v in synth.c4_batch(sizes=sizes)]
+    bp = drt.BatchPlan(sizes)
+    outs = bp.bind(vols)
+    bp.run()
+    assert bp.device_error() == 0
+    checked = 0
+    for i, (v, o, N) in enumerate(zip(vols, outs, sizes)):
+        assert torch.equal(o, drt.planes_forward(v)), f"volume {i} (N={N})"
+        if N == 16 and checked < 3:
+            np.testing.assert_array_equal(o.cpu().numpy(), oracle_mod.planes_forward(v.cpu().numpy()))
+            checked += 1
+
+
+def test_batched_launch_replays_in_a_cuda_graph(drt):
+    Ns = [32, 64, 16]
+    vols = _vols(Ns, 80)
+    bp = drt.BatchPlan(Ns)
+    outs = bp.bind(vols)
+    want = [drt.planes_forward(v) for v in vols]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        bp.run()  # warm-up outside capture
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    for o in outs:
+        o.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        bp.run()
+    for _ in range(2):
+        for o in outs:
+            o.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for o, w in zip(outs, want):
+            assert torch.equal(o, w)
+    assert bp.device_error() == 0
+
+
+def test_withheld_signal_times_out_without_a_fault(drt):
+    """A first-pass completion signal that never arrives: the dependent waits
+    give up after the limit, the launch ends and reports DRT3D_ERR_TIMEOUT;
+    the plan works again once the hook is cleared."""
+    Ns = [64, 32]
+    vols = _vols(Ns, 90)
+    bp = drt.BatchPlan(Ns)
+    outs = bp.bind(vols)
+    bp.set_wait_limit(2_000_000, withhold_vol=0, withhold_dodecant=3)  # 2 ms
+    bp.run()
+    assert bp.device_error() == 7  # DRT3D_ERR_TIMEOUT
+    bp.set_wait_limit(2_000_000_000)
+    bp.run()
+    assert bp.device_error() == 0
+    for v, o in zip(vols, outs):
+        assert torch.equal(o, drt.planes_forward(v))
