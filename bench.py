@@ -45,6 +45,8 @@ def parse_args(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched / lines / lsq side measurements")
+    ap.add_argument("--no-tune", action="store_true", help="use the default stage-fusion split")
     return ap.parse_args(argv)
 
 
@@ -144,6 +146,33 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash() -> str:
+    """sha256 of the CUDA sources (a stored ncu traffic figure is only valid for them)."""
+    import glob
+    import hashlib
+
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2501_13664_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(os.path.basename(p).encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from profiles/ncu_traffic.json, or None
+    when absent or taken on other kernel sources."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_sha256") != kernel_source_hash():
+        return None
+    e = d.get("kernels", {}).get(kernel)
+    return None if e is None else float(e["dram_bytes_per_launch"])
 
 
 def measured_peaks() -> dict:
@@ -249,6 +278,12 @@ def run_ours(args):
     f_np = synth.c2_volume(N, seed=2 + rank)
     vol = torch.from_numpy(f_np).to(dev)
     plan = drt3d.get_plan(N, torch.uint8)
+    tuned = {}
+    if not args.no_tune:
+        from paper_2501_13664_gb300 import autotune
+
+        tuned = autotune.tune([N] + ([] if args.no_extras else sorted(set(synth.c4_sizes()))))
+        plan.set_schedule(tuned[N])
     out = torch.empty((12, N, N, 3 * N), dtype=torch.int32, device=dev)
     ws = plan.workspace("planes_forward")
     inv_k = 0
@@ -327,9 +362,10 @@ def run_ours(args):
             "N": N, "dodecants": 12, "input_dtype": "u8",
             "l2": "flushed between timed steps by writing a 258 MB buffer (untimed)",
             "inverse_in_step": have_inverse,
+            "schedule": list(plan.schedule()),
         },
         "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peaks["hbm_gbs"],
-                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic(dom_name),
                      "peak_source": peaks["source"], "avg_ms": dom_ms, "algo_bytes_per_launch": dom_bytes},
         "hbm_floor_gbs": floor_bytes / (ms / 1000.0) / 1e9,
         "kernels": kernels,
@@ -361,6 +397,16 @@ def run_ours(args):
                        "h2d_bytes_per_step": int(pin_in.numel()),
                        "d2h_bytes_per_step": int(pin_out.numel() * 4 + (pin_inv.numel() * 4 if have_inverse else 0))}
 
+    if not args.no_extras:
+        del out, ws, flush
+        torch.cuda.empty_cache()
+        line["batched_c4"] = bench_batched(drt3d, synth, dev, tuned)
+        torch.cuda.empty_cache()
+        line["lines_c3"] = bench_lines(drt3d, synth, dev)
+        torch.cuda.empty_cache()
+        line["lsq_c5"] = bench_lsq(drt3d, synth, dev)
+        torch.cuda.empty_cache()
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_cpu, sample = oracle_volume_seconds(f_np)
         line["cpu_baseline"] = {"value": 1.0 / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -372,6 +418,102 @@ def run_ours(args):
 
         dist.destroy_process_group()
     return 0
+
+
+def _event_ms(fn, reps: int) -> list:
+    import torch
+
+    out = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        out.append(a.elapsed_time(b))
+    return out
+
+
+def bench_batched(drt3d, synth, dev, tuned) -> dict:
+    """Config 4: 96 uint8 volumes of uneven N, one persistent launch replayed
+    from a CUDA graph vs 96 one-by-one forward calls on one stream."""
+    import torch
+
+    sizes = synth.c4_sizes()
+    vols = [torch.from_numpy(v).to(dev) for v in synth.c4_batch(sizes=sizes)]
+    sched = {N: tuple(tuned[N]) for N in set(sizes) if N in tuned}
+    bp = drt3d.BatchPlan(sizes, schedules=sched)
+    outs = bp.bind(vols)
+    plans, wss = {}, {}
+    for N in set(sizes):
+        p = drt3d.get_plan(N, torch.uint8)
+        if N in sched:
+            p.set_schedule(sched[N])
+        plans[N] = p
+        wss[N] = p.workspace("planes_forward")
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        bp.run()
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        bp.run()
+    assert bp.device_error() == 0
+
+    def one_by_one():
+        for v, o, N in zip(vols, outs, sizes):
+            drt3d.planes_forward(v, drt3d.ALL, out=o, workspace=wss[N])
+
+    for _ in range(3):
+        g.replay()
+        one_by_one()
+    tb = sorted(_event_ms(g.replay, 7))[3]
+    t1 = sorted(_event_ms(one_by_one, 7))[3]
+    floor = sum(12.0 * N * N * (3 * N - 2) * 4 + N ** 3 for N in sizes)
+    return {"volumes": len(sizes), "batched_ms": tb, "one_by_one_ms": t1,
+            "batched_volumes_per_s": len(sizes) / (tb / 1000), "one_by_one_volumes_per_s": len(sizes) / (t1 / 1000),
+            "speedup": t1 / tb, "floor_gbs_batched": floor / (tb / 1000) / 1e9,
+            "launches_batched": 1, "launches_one_by_one": sum(len(plans[N].schedule()) for N in sizes),
+            "note": "batched = one memset + one persistent kernel, replayed from a CUDA graph; median of 7"}
+
+
+def bench_lines(drt3d, synth, dev) -> dict:
+    """Config 3: DJT of lines, N=128 int16, all 12 sectors (51.5 GB out)."""
+    import torch
+
+    N = 128
+    vol = torch.from_numpy(synth.c3_volume(N)).to(dev)
+    plan = drt3d.get_plan(N, torch.int16)
+    out = torch.empty((12, N, N, 2 * N, 2 * N), dtype=torch.int32, device=dev)
+    ws = plan.workspace("lines_forward")
+    run = lambda: drt3d.lines_forward(vol, drt3d.ALL, out=out, workspace=ws)  # noqa: E731
+    run()
+    t = sorted(_event_ms(run, 5))[2]
+    floor = 12.0 * N * N * (2 * N) * (2 * N) * 4 + N ** 3 * 2
+    del out
+    return {"ms": t, "sectors_per_s": 12 / (t / 1000), "floor_gbs": floor / (t / 1000) / 1e9,
+            "workload": "N=128 int16 uniform 0..1023 + 32 lines, 12 sectors, int32 out"}
+
+
+def bench_lsq(drt3d, synth, dev) -> dict:
+    """Config 5: one gradient step of the least-squares fit, 8 x 128^3 float32."""
+    import torch
+
+    N, B = 128, 8
+    x = torch.from_numpy(synth.c5_batch(N=N, batch=B)).to(dev)
+    b = torch.zeros((B, 12, N, N, 3 * N), dtype=torch.float32, device=dev)
+
+    def step():
+        xr = x.detach().requires_grad_(True)
+        r = drt3d.planes(xr) - b
+        (0.5 * (r * r).sum()).backward()
+        return xr.grad
+
+    step()
+    t = sorted(_event_ms(step, 5))[2]
+    return {"ms_per_step": t, "volumes": B, "N": N,
+            "note": "forward (12 dodecants) + loss + hand-written adjoint via autograd, per step of 8 volumes"}
 
 
 def main(argv=None):

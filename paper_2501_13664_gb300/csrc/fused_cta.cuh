@@ -72,11 +72,21 @@ struct Chunks32 { uint4 c[2]; };   // 8 x 32-bit
 template <typename TIn>
 using ChunksOf = typename std::conditional<sizeof(TIn) == 2, Chunks16, Chunks32>::type;
 
+// Global loads: the read-only path, or (COHERENT) an L2-coherent load.  Both
+// name the global space explicitly, so pointers that come from a table in
+// memory (not kernel parameters) still compile to global accesses.
 template <typename V, bool COHERENT>
 __device__ __forceinline__ V ld_vec(const V* p) {
-    if constexpr (COHERENT) return *p;
+    if constexpr (COHERENT) return __ldcg(p);
     else return __ldg(p);
 }
+
+// Global stores with the address space named explicitly.
+__device__ __forceinline__ void st_global(uint4* p, uint4 v) { __stcg(p, v); }
+__device__ __forceinline__ void st_global(uint2* p, uint2 v) { __stcg(p, v); }
+__device__ __forceinline__ void st_global(uint32_t* p, uint32_t v) { __stcg(p, v); }
+__device__ __forceinline__ void st_global(uint16_t* p, uint16_t v) { __stcg(reinterpret_cast<unsigned short*>(p), v); }
+__device__ __forceinline__ void st_global(float* p, float v) { __stcg(p, v); }
 
 template <typename TIn, bool COHERENT>
 __device__ __forceinline__ ChunksOf<TIn> load_chunks(const TIn* row, int base, int dmax, int q) {
@@ -150,16 +160,16 @@ __device__ __forceinline__ void store_rows(const FusedLaunch& L, const FusedSlot
             if constexpr (sizeof(TOut) == 4) {
                 uint4 w;
                 memcpy(&w, e, 16);
-                *reinterpret_cast<uint4*>(dst) = w;
+                st_global(reinterpret_cast<uint4*>(dst), w);
             } else {
                 uint2 w;
                 memcpy(&w, e, 8);
-                *reinterpret_cast<uint2*>(dst) = w;
+                st_global(reinterpret_cast<uint2*>(dst), w);
             }
         } else {
 #pragma unroll
             for (int i = 0; i < K; ++i)
-                if (p0 + i < L.V && d + i < L.dmax) dst[i] = (TOut)v[t2][i];
+                if (p0 + i < L.V && d + i < L.dmax) st_global(dst + i, (TOut)v[t2][i]);
         }
     }
 }

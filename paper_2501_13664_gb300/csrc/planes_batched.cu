@@ -1,10 +1,11 @@
 // planes_batched.cu -- the planes forward transform of many volumes of
 // different sizes in one persistent launch.
 //
-// Work items are the CTAs of every fused pass of every volume and dodecant
-// (see planes_fused.cu).  They are numbered pass-major: all first-pass items
-// of all volumes, then all second-pass items, ...; within a (pass, volume)
-// segment item i is dodecant slot i / ctas, unit-tile i % ctas.  Resident
+// Work items are the units of every fused pass of every volume and dodecant
+// (see planes_fused.cu), each with all its displacement tiles.  They are
+// numbered pass-major: all first-pass items of all volumes, then all
+// second-pass items, ...; within a (pass, volume) segment item i is dodecant
+// slot i / units, unit i % units.  Resident
 // CTAs (two per SM) take items from an atomic counter.  An item of pass p > 0
 // reads the intermediate written by every pass p-1 item of its (volume,
 // dodecant); those items were all handed out before it, to CTAs that are
@@ -31,7 +32,7 @@ struct BatchVol {
     int npass;
     int G[kBatchMaxPass];
     int in_kind[kBatchMaxPass], out_kind[kBatchMaxPass];
-    unsigned ctas[kBatchMaxPass];  // items per dodecant slot
+    unsigned ctas[kBatchMaxPass];  // items (units, each all its tiles) per dodecant slot
 };
 
 struct BatchArgs {
@@ -77,9 +78,29 @@ __device__ bool wait_counter(const BatchArgs& A, const unsigned* ctr, unsigned t
     }
 }
 
+// The item's pass header and dodecant slot are copied into registers: read
+// through a global pointer, the compiler would have to reload them after every
+// store (it cannot prove the output buffers do not alias the tables).
 template <typename TIn, typename TOut, typename TS, int G, bool INGEST>
-__device__ __forceinline__ void run_g(const FusedLaunch& L, int slot, unsigned cta, unsigned char* smem) {
-    fused_cta<TIn, TOut, uint32_t, TS, G, INGEST, true>(L, L.slot[slot], cta, smem);
+__device__ __forceinline__ void run_g(const FusedLaunch& Lg, int slot, unsigned cta, unsigned char* smem) {
+    FusedLaunch L;
+    L.N = Lg.N;
+    L.n = Lg.n;
+    L.m0 = Lg.m0;
+    L.gin = Lg.gin;
+    L.gout = Lg.gout;
+    L.dmax = Lg.dmax;
+    L.V = Lg.V;
+    L.ntiles = Lg.ntiles;
+    L.ctas = Lg.ctas;
+    L.vec_store = Lg.vec_store;
+    const FusedSlot sp = Lg.slot[slot];
+    // one item = one unit: all its displacement tiles
+    const unsigned nt = (unsigned)L.ntiles;
+    for (unsigned t = 0; t < nt; ++t) {
+        if (t > 0) __syncthreads();  // the previous tile's phase 2 is done with shared memory
+        fused_cta<TIn, TOut, uint32_t, TS, G, INGEST, true>(L, sp, cta * nt + t, smem);
+    }
 }
 
 template <typename TIn, typename TOut, typename TS, bool INGEST>
@@ -93,24 +114,34 @@ __device__ __forceinline__ void run_kind(const FusedLaunch& L, int G, int slot, 
 
 __global__ void __launch_bounds__(256, 2) planes_batched(const __grid_constant__ BatchArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ unsigned s_item;
-    __shared__ int s_go;
+    __shared__ unsigned s_item, s_next;
+    __shared__ int s_go, s_seg;
+    // The next item is claimed while the current one runs, hiding the
+    // atomic's round trip.  A CTA's items only increase, so its segment is
+    // found by advancing a cursor (amortised O(1)).
+    int seg = 0;  // thread 0's cursor
+    if (threadIdx.x == 0) s_next = atomicAdd(A.next, 1u);
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(A.next, 1u);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned it = s_next;
+            s_item = it;
+            if (it < A.nitems) {
+                s_next = atomicAdd(A.next, 1u);
+                while (__ldg(A.seg_start + seg + 1) <= it) ++seg;
+                s_seg = seg;
+            }
+        }
         __syncthreads();
         const unsigned item = s_item;
         if (item >= A.nitems) return;
-        int lo = 0, hi = A.nseg - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (A.seg_start[mid] <= item) lo = mid;
-            else hi = mid - 1;
-        }
-        const int v = A.seg_vol[lo], p = A.seg_pass[lo];
+        const int lo = s_seg;
+        const int v = __ldg(A.seg_vol + lo), p = __ldg(A.seg_pass + lo);
         const BatchVol& B = A.vols[v];
-        const unsigned local = item - A.seg_start[lo];
-        const int slot = (int)(local / B.ctas[p]);
-        const unsigned cta = local % B.ctas[p];
+        const unsigned local = item - __ldg(A.seg_start + lo);
+        const unsigned ctas_p = B.ctas[p];
+        const int slot = (int)(local / ctas_p);
+        const unsigned cta = local - (unsigned)slot * ctas_p;
         unsigned* done = A.done + ((size_t)v * kMaxSlots + slot) * kBatchMaxPass;
         if (p > 0) {
             if (threadIdx.x == 0) s_go = wait_counter(A, done + (p - 1), B.ctas[p - 1]) ? 1 : 0;
@@ -129,10 +160,13 @@ __global__ void __launch_bounds__(256, 2) planes_batched(const __grid_constant__
         } else {
             run_kind<uint32_t, uint32_t, uint32_t, false>(L, G, slot, cta, smem);
         }
-        __syncthreads();
-        if (threadIdx.x == 0 && !(p == 0 && v == A.withhold_vol && slot == A.withhold_slot)) {
-            __threadfence();
-            atomicAdd(done + p, 1u);
+        // Signal completion only where a later pass depends on it.
+        if (p + 1 < B.npass) {
+            __syncthreads();
+            if (threadIdx.x == 0 && !(p == 0 && v == A.withhold_vol && slot == A.withhold_slot)) {
+                __threadfence();
+                atomicAdd(done + p, 1u);
+            }
         }
     }
 }
@@ -318,7 +352,7 @@ drt3d_status drt3d_batch_bind(drt3d_batch_plan* B, const drt3d_vol_desc* descs, 
             bv.G[p] = ps.G;
             bv.in_kind[p] = (int)ps.in_kind;
             bv.out_kind[p] = (int)ps.out_kind;
-            bv.ctas[p] = (unsigned)L.ctas;
+            bv.ctas[p] = (unsigned)(L.ctas / L.ntiles);
         }
         ws += align_up(vol_ws_bytes(S), 256);
     }
