@@ -392,6 +392,7 @@ drt3d_status drt3d_planes_forward(const drt3d_plan* P, const void* d_in, void* d
     L.N = N;
     L.n = P->n;
     L.dmax = 3 * N;
+    L.status = P->d_status;
     for (int p = 0; p < S.npass; ++p) {
         const FusedPass& ps = S.pass[p];
         int i = 0;
@@ -414,12 +415,16 @@ drt3d_status drt3d_planes_forward(const drt3d_plan* P, const void* d_in, void* d
         L.ntiles = (3 * N - ps.out.base + L.V - 1) / L.V;
         const long long per_axis = 1LL << (P->n - ps.G);
         L.ctas = per_axis * per_axis * L.ntiles;
-        L.vec_store = (ps.out.pitch % 4 == 0) && (ps.out.base % 4 == 0);
+        L.vec_store = (ps.out.pitch % 4 == 0) && (ps.out.base % 4 == 0) && (3 * N) % 4 == 0;
         char nm[40];
         std::snprintf(nm, sizeof nm, "planes_fused G=%d m0=%d", ps.G, ps.m0);
         prof_begin(P, stream, nm, nslots * fused_pass_bytes(P, ps));
-        if (launch_planes_fused(L, ps.G, ps.in_kind, ps.out_kind, ps.ingest, nslots, stream) != cudaSuccess)
-            return DRT3D_ERR_CUDA;
+        cudaError_t e;
+        if (fused_uses_tma(ps.G, ps.in_kind, ps.ingest))
+            e = launch_planes_fused_tma(L, ps.G, ps.out_kind, L.slot[0].in, 2 * buf, nslots, stream);
+        else
+            e = launch_planes_fused(L, ps.G, ps.in_kind, ps.out_kind, ps.ingest, nslots, stream);
+        if (e != cudaSuccess) return DRT3D_ERR_CUDA;
         prof_end(P, stream);
     }
     return DRT3D_OK;

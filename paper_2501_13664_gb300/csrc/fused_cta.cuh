@@ -7,6 +7,7 @@
 #include <type_traits>
 
 #include "internal.cuh"
+#include "tma.cuh"
 #include "warp_drt.cuh"
 
 namespace drt3d {
@@ -58,6 +59,17 @@ template <int G> __host__ __device__ constexpr int fused_warps() { return G >= 3
 // outputs plus the 2^G - 1 the phase-2 shifts reach past them.
 template <int G> __host__ __device__ constexpr int fused_v() { return (WT - 2 * ((1 << G) - 1)) & ~3; }
 template <int G> __host__ __device__ constexpr int fused_ws() { return (fused_v<G>() + (1 << G) - 1 + 3) & ~3; }
+
+// Staged (TMA) input of one phase-1 group: 2^G rows of WT + 8 16-bit
+// elements, the window [q, q + WT) of a row rounded out to 8-element (16-byte)
+// boundaries.  Each staged row starts 128 bytes after the previous one; the
+// staging of group u2 sits inside that group's block of phase-1 results,
+// which overwrites it once the group's warp has read it.
+constexpr int kStageElems = WT + 8;
+constexpr int kStageRowBytes = 384;
+// Upper bound on a stalled transaction-count wait (ns): a load that has not
+// landed by then is reported as a time-out.
+constexpr unsigned long long kTmaWaitNs = 200000000ull;
 
 // Buffer rows are stored on [base, base + pitch) with base and pitch
 // multiples of 8 and hold zeros outside [base, dmax) (dmax a multiple of 4).
@@ -136,24 +148,70 @@ __device__ __forceinline__ void extract4(const ChunksOf<TIn>& w, int r, T (&v)[K
     }
 }
 
+// 16-bit buffer input of phase 1.  A row's window [q, q + 4) lies in the
+// two aligned 4-element chunks starting at q & ~3; `lo` is the offset of the
+// first chunk from the row's first stored element and `width` the stored
+// width (both multiples of 4).  A chunk outside [0, width) reads as zero, so
+// each chunk is one predicated load.  The in-chunk offset q & 3 is the same
+// for all lanes and repeats with u1 mod 4, so rows are loaded by residue
+// class, and the window is unpacked with its offset fixed at compile time.
+template <bool COHERENT>
+__device__ __forceinline__ Chunks16 load_pair_u16(const uint16_t* c0, int lo, int width) {
+    Chunks16 w;
+    w.c[0] = make_uint2(0u, 0u);
+    w.c[1] = make_uint2(0u, 0u);
+    if ((unsigned)lo < (unsigned)width) w.c[0] = ld_vec<uint2, COHERENT>(reinterpret_cast<const uint2*>(c0));
+    if ((unsigned)(lo + 4) < (unsigned)width) w.c[1] = ld_vec<uint2, COHERENT>(reinterpret_cast<const uint2*>(c0 + 4));
+    return w;
+}
+
+template <int RR, typename T>
+__device__ __forceinline__ void unpack_u16(const Chunks16& w, T (&v)[K]) {
+    const uint32_t x[4] = {w.c[0].x, w.c[0].y, w.c[1].x, w.c[1].y};
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const int e = RR + i;  // element of the 8 loaded
+        const uint32_t word = x[e >> 1];
+        v[i] = to_acc<uint16_t, T>((uint16_t)((e & 1) ? (word >> 16) : (word & 0xFFFFu)));
+    }
+}
+
+template <int J, int G, typename T>
+__device__ __forceinline__ void unpack_class_u16(int rr, const Chunks16 (&w)[1 << G], T (&v)[1 << G][K]) {
+#define DRT3D_UNPACK_CLASS(RRV)                                  \
+    _Pragma("unroll") for (int u1 = J; u1 < (1 << G); u1 += 4) \
+        unpack_u16<RRV, T>(w[u1], v[u1]);
+    switch (rr) {
+    case 0: DRT3D_UNPACK_CLASS(0) break;
+    case 1: DRT3D_UNPACK_CLASS(1) break;
+    case 2: DRT3D_UNPACK_CLASS(2) break;
+    default: DRT3D_UNPACK_CLASS(3) break;
+    }
+#undef DRT3D_UNPACK_CLASS
+}
+
 // Phase-2 store of output rows (t1, t2), t2 < 2^G, over the tile's first V
-// displacements: aligned vector stores where a lane's K values are all valid.
+// displacements.  d0, V, base and dmax are multiples of 4, so a lane's K = 4
+// values are either all valid or all past the tile: lanes past it return at
+// once, the others store one aligned vector per row (element stores only when
+// the output pitch rules vectors out).
 template <typename TOut, typename T, int G>
 __device__ __forceinline__ void store_rows(const FusedLaunch& L, const FusedSlot& sp, const T (&v)[1 << G][K],
                                            int t1, int sg1, int wq1, int sg2, int wq2, int rs1, int rs2,
                                            int d0, int lane) {
     constexpr int R = 1 << G;
-    const int m0 = L.m0;
-    const int o1 = t1 + (sg1 << G) + (wq1 << (m0 + G));
-    TOut* out = static_cast<TOut*>(sp.out);
     const int p0 = lane * K;
     const int d = d0 + p0;
-    const bool full = (p0 + K <= L.V) && (d + K <= L.dmax) && L.vec_store;
+    if (p0 >= L.V || d >= L.dmax) return;
+    const int m0 = L.m0;
+    const int o1 = t1 + (sg1 << G) + (wq1 << (m0 + G));
+    TOut* out = static_cast<TOut*>(sp.out) + (d - L.gout.base);
     const long long orow0 = (long long)o1 * rs1 + (long long)((sg2 << G) + (wq2 << (m0 + G))) * rs2;
+    const long long rstride = (long long)rs2 * L.gout.pitch;
+    TOut* dst = out + orow0 * L.gout.pitch;
+    if (L.vec_store) {
 #pragma unroll
-    for (int t2 = 0; t2 < R; ++t2) {
-        TOut* dst = out + (orow0 + (long long)t2 * rs2) * L.gout.pitch + (d - L.gout.base);
-        if (full) {
+        for (int t2 = 0; t2 < R; ++t2, dst += rstride) {
             TOut e[K];
 #pragma unroll
             for (int i = 0; i < K; ++i) e[i] = (TOut)v[t2][i];
@@ -166,11 +224,13 @@ __device__ __forceinline__ void store_rows(const FusedLaunch& L, const FusedSlot
                 memcpy(&w, e, 8);
                 st_global(reinterpret_cast<uint2*>(dst), w);
             }
-        } else {
+        }
+    } else {
+#pragma unroll
+        for (int t2 = 0; t2 < R; ++t2, dst += rstride)
 #pragma unroll
             for (int i = 0; i < K; ++i)
-                if (p0 + i < L.V && d + i < L.dmax) st_global(dst + i, (TOut)v[t2][i]);
-        }
+                if (d + i < L.dmax) st_global(dst + i, (TOut)v[t2][i]);
     }
 }
 
@@ -179,14 +239,17 @@ __device__ __forceinline__ void store_rows(const FusedLaunch& L, const FusedSlot
 // idle.  With COHERENT the input is read with plain loads instead of the
 // read-only path (the batched kernel reads buffers other CTAs of the same
 // launch wrote).
-template <typename TIn, typename TOut, typename T, typename TS, int G, bool INGEST, bool COHERENT>
+template <typename TIn, typename TOut, typename T, typename TS, int G, bool INGEST, bool COHERENT, bool TMA = false>
 __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot& sp, unsigned cta,
-                                          unsigned char* smem_raw) {
+                                          unsigned char* smem_raw, const CUtensorMap* tmap = nullptr,
+                                          int slot_z = 0, uint64_t* mbar = nullptr) {
+    static_assert(!TMA || (sizeof(TIn) == 2 && !INGEST && sizeof(TS) == 4 && G >= 3),
+                  "TMA staging: 16-bit buffer input, 32-bit phase-1 results, G >= 3");
     constexpr int R = 1 << G;
     constexpr int NW = fused_warps<G>();
     constexpr int GPW = R / NW > 0 ? R / NW : 1;  // row groups per warp
     constexpr int WS = fused_ws<G>();
-    TS* S = reinterpret_cast<TS*>(smem_raw);  // [t1][u2][WS] (+ K pad)
+    TS* S = reinterpret_cast<TS*>(smem_raw);  // [u2][t1][WS] (+ K pad)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool active = warp < NW;
     const int m0 = L.m0;
@@ -223,6 +286,37 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
             store_rows<TOut, T, G>(L, sp, v, t1, sg1, wq1, sg2, wq2, rs1, rs2, d0, lane);
         }
         return;
+    }
+
+    if constexpr (TMA) {
+        // Stage every group's rows: one 1-row box per (u2, u1); a group whose
+        // windows all miss the stored range issues nothing (its warp parks
+        // zeros below, the same test decides both).
+        if (threadIdx.x == 0) {
+#pragma unroll 1
+            for (int g = 0; g < R; ++g) tma::mbar_init(&mbar[g], 1);
+            tma::fence_barrier_init();
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll 1
+            for (int gi = 0; gi < GPW; ++gi) {
+                const int u2 = warp + gi * NW;
+                const int g_lo = d0 + sg2 * u2, g_hi = g_lo + sg1 * (R - 1) + WT + 4;
+                if (g_hi <= L.gin.base || g_lo >= L.dmax) continue;
+                if (lane == 0) tma::mbar_arrive_expect_tx(&mbar[u2], R * kStageElems * 2);
+                __syncwarp();
+                if (lane < R) {
+                    const int u1 = lane;
+                    const int a2 = sg2 + (u2 << m0) + (wq2 << (m0 + G));
+                    const long long row =
+                        (long long)(sg1 + (wq1 << (m0 + G))) * rs1 + (long long)a2 * rs2 + (long long)(u1 * rs1 << m0);
+                    const int q = g_lo + sg1 * u1;
+                    unsigned char* dst = smem_raw + (size_t)u2 * R * WS * sizeof(TS) + u1 * kStageRowBytes;
+                    tma::load_3d(dst, tmap, (q & ~7) - L.gin.base, (int)row, slot_z, &mbar[u2]);
+                }
+            }
+        }
     }
 
     // ---------------- phase 1: transform along axis 1, warp = u2 ----------
@@ -288,7 +382,7 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
                 if (lane * K < WS) {
 #pragma unroll
                     for (int t1 = 0; t1 < R; ++t1) {
-                        TS* dst = S + ((t1 * R + u2) * WS + lane * K);
+                        TS* dst = S + ((u2 * R + t1) * WS + lane * K);
 #pragma unroll
                         for (int i = 0; i < K; ++i) dst[i] = TS(0);
                     }
@@ -298,21 +392,58 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
             const TIn* buf = static_cast<const TIn*>(sp.in);
             const long long row0 = (long long)(sg1 + (wq1 << (m0 + G))) * rs1 + (long long)a2 * rs2;
             const long long rstep = (long long)rs1 << m0;  // rows between u1 and u1 + 1
-            // Issue the loads of up to 16 x 16-bit or 8 x 32-bit rows, then extract.
-            constexpr int BATCH = sizeof(TIn) == 2 ? R : (R < 8 ? R : 8);
-#pragma unroll
-            for (int b0 = 0; b0 < R; b0 += BATCH) {
-                ChunksOf<TIn> w[BATCH];
-#pragma unroll
-                for (int j = 0; j < BATCH; ++j) {
-                    const int u1 = b0 + j;
-                    const TIn* rowp = buf + (row0 + u1 * rstep) * L.gin.pitch;
-                    w[j] = load_chunks<TIn, COHERENT>(rowp, L.gin.base, L.dmax, start + sg1 * u1);
+            if constexpr (TMA) {
+                // Wait for the group's staged rows, then read each lane's 4
+                // elements at the row's offset inside its 16-byte-aligned box.
+                if (!tma::mbar_wait(&mbar[u2], 0, kTmaWaitNs)) {
+                    if (lane == 0 && L.status) atomicCAS(L.status, 0, (int)DRT3D_ERR_TIMEOUT);
                 }
+                const uint16_t* st = reinterpret_cast<const uint16_t*>(smem_raw + (size_t)u2 * R * WS * sizeof(TS));
+                const int g_lo = d0 + sg2 * u2;
 #pragma unroll
-                for (int j = 0; j < BATCH; ++j) {
-                    const int u1 = b0 + j;
-                    extract4<TIn, T>(w[j], (start + sg1 * u1) & 3, v[u1]);
+                for (int u1 = 0; u1 < R; ++u1) {
+                    const uint16_t* src = st + u1 * (kStageRowBytes / 2) + ((g_lo + sg1 * u1) & 7) + lane * K;
+#pragma unroll
+                    for (int i = 0; i < K; ++i) v[u1][i] = to_acc<uint16_t, T>(src[i]);
+                }
+                __syncwarp();  // the group's results overwrite its staging
+            } else if constexpr (sizeof(TIn) == 2) {
+                const int L0 = start - L.gin.base;  // window offset of row u1 = 0
+                const int width = L.dmax - L.gin.base;
+                const long long step = rstep * L.gin.pitch + sg1;  // window step per u1
+                const uint16_t* q0 = reinterpret_cast<const uint16_t*>(buf) + row0 * L.gin.pitch + L0;
+                const int a = sg1 & 3, c = L0 & 3;
+                Chunks16 w[R];
+#pragma unroll
+                for (int j = 0; j < (R < 4 ? R : 4); ++j) {
+                    const int rr = (c + a * j) & 3;
+                    const uint16_t* pj = q0 + (long long)j * step - rr;
+                    const int lo_j = L0 + j * sg1 - rr;
+#pragma unroll
+                    for (int u1 = j; u1 < R; u1 += 4)
+                        w[u1] = load_pair_u16<COHERENT>(pj + (long long)(u1 - j) * step, lo_j + (u1 - j) * sg1, width);
+                }
+                unpack_class_u16<0, G>(c, w, v);
+                if constexpr (R > 1) unpack_class_u16<1, G>((c + a) & 3, w, v);
+                if constexpr (R > 2) unpack_class_u16<2, G>((c + 2 * a) & 3, w, v);
+                if constexpr (R > 3) unpack_class_u16<3, G>((c + 3 * a) & 3, w, v);
+            } else {
+                // Issue the loads of up to 8 x 32-bit rows, then extract.
+                constexpr int BATCH = R < 8 ? R : 8;
+#pragma unroll
+                for (int b0 = 0; b0 < R; b0 += BATCH) {
+                    ChunksOf<TIn> w[BATCH];
+#pragma unroll
+                    for (int j = 0; j < BATCH; ++j) {
+                        const int u1 = b0 + j;
+                        const TIn* rowp = buf + (row0 + u1 * rstep) * L.gin.pitch;
+                        w[j] = load_chunks<TIn, COHERENT>(rowp, L.gin.base, L.dmax, start + sg1 * u1);
+                    }
+#pragma unroll
+                    for (int j = 0; j < BATCH; ++j) {
+                        const int u1 = b0 + j;
+                        extract4<TIn, T>(w[j], (start + sg1 * u1) & 3, v[u1]);
+                    }
                 }
             }
         }
@@ -320,7 +451,7 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
         if (lane * K < WS) {
 #pragma unroll
             for (int t1 = 0; t1 < R; ++t1) {
-                TS* dst = S + ((t1 * R + u2) * WS + lane * K);
+                TS* dst = S + ((u2 * R + t1) * WS + lane * K);
                 TS e[K];
 #pragma unroll
                 for (int i = 0; i < K; ++i) e[i] = (TS)v[t1][i];
@@ -346,7 +477,7 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
 #pragma unroll
         for (int u2 = 0; u2 < R; ++u2) {
             // lanes past WS read the next row (or the pad): values they feed are invalid
-            const TS* src = S + ((t1 * R + u2) * WS + lane * K);
+            const TS* src = S + ((u2 * R + t1) * WS + lane * K);
             TS e[K];
             if constexpr (sizeof(TS) == 4) {
                 uint4 w = *reinterpret_cast<const uint4*>(src);

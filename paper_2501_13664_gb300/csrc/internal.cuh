@@ -133,6 +133,7 @@ struct FusedLaunch {
     int ntiles;
     long long ctas;  // CTAs per slot
     int vec_store;   // output rows allow aligned vector stores
+    int* status;     // device status word (time-outs of staged loads), may be null
 };
 
 // One fused pass: G stages of eq.(map3D) (both axes).
@@ -169,7 +170,7 @@ struct InvLaunch {
     int lo_out;       // values below this displacement must vanish after the pass
     int scatter;      // last pass: write the volume through the dodecant map
 };
-size_t inverse_smem_bytes(int N, int G, int base);
+size_t inverse_smem_bytes(int N, int G, int base, int m0);
 cudaError_t launch_planes_inverse_pass(const InvLaunch& L, int G, cudaStream_t s);
 
 // One pass of the lines transform (djt.cu).
@@ -196,6 +197,12 @@ cudaError_t launch_djt_pass(const DjtLaunch& L, int G, int K, drt3d_dtype in_dty
 int fused_valid(int G);  // valid displacements per CTA tile of a G-stage fused pass
 cudaError_t launch_planes_fused(const FusedLaunch& L, int G, ElemKind in_kind, ElemKind out_kind,
                                 bool ingest, int nslots, cudaStream_t s);
+// Whether a fused pass stages its input through TMA boxes (16-bit buffer
+// input, G >= 3), and that launch: `in_base` is slot 0's input buffer, the
+// other slots follow at `slot_stride` bytes.
+bool fused_uses_tma(int G, ElemKind in_kind, bool ingest);
+cudaError_t launch_planes_fused_tma(const FusedLaunch& L, int G, ElemKind out_kind, const void* in_base,
+                                    size_t slot_stride, int nslots, cudaStream_t s);
 cudaError_t launch_planes_pass(const PassLaunch& L, int G, drt3d_dtype in_dtype, bool ingest,
                                bool is_float, int nslots, cudaStream_t s);
 cudaError_t launch_planes_adjoint_pass(const PassLaunch& L, int G, bool scatter, bool is_float,

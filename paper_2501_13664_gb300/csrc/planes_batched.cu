@@ -94,6 +94,7 @@ __device__ __forceinline__ void run_g(const FusedLaunch& Lg, int slot, unsigned 
     L.ntiles = Lg.ntiles;
     L.ctas = Lg.ctas;
     L.vec_store = Lg.vec_store;
+    L.status = nullptr;
     const FusedSlot sp = Lg.slot[slot];
     // one item = one unit: all its displacement tiles
     const unsigned nt = (unsigned)L.ntiles;
@@ -338,7 +339,7 @@ drt3d_status drt3d_batch_bind(drt3d_batch_plan* B, const drt3d_vol_desc* descs, 
             L.ntiles = (3 * N - ps.out.base + L.V - 1) / L.V;
             const long long per_axis = 1LL << (L.n - ps.G);
             L.ctas = per_axis * per_axis * L.ntiles;
-            L.vec_store = (ps.out.pitch % 4 == 0) && (ps.out.base % 4 == 0);
+            L.vec_store = (ps.out.pitch % 4 == 0) && (ps.out.base % 4 == 0) && (3 * N) % 4 == 0;
             for (int k = 0; k < 12; ++k) {
                 char* bufA = ws + (size_t)k * 2 * buf;
                 char* bufB = bufA + buf;

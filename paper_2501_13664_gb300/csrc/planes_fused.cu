@@ -53,6 +53,55 @@ cudaError_t launch_g(const FusedLaunch& L, int nslots, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Pass over 16-bit buffer rows with the phase-1 input staged by TMA: one
+// 1-row box per (u2, u1) row window, landing in the group's block of
+// phase-1 results; one mbarrier per group counts the bytes.
+template <typename TOut, int G>
+__global__ void __launch_bounds__(32 * fused_warps<G>(), (G >= 4 ? 2 : 1))
+planes_fused_tma(const __grid_constant__ FusedLaunch L, const __grid_constant__ CUtensorMap tmap) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar[1 << G];
+    // TMA destinations are kept 128-byte aligned.
+    unsigned char* sm = smem_raw + ((128u - (tma::smem_u32(smem_raw) & 127u)) & 127u);
+    fused_cta<uint16_t, TOut, uint32_t, uint32_t, G, false, false, true>(L, L.slot[blockIdx.y], blockIdx.x, sm,
+                                                                        &tmap, (int)blockIdx.y, mbar);
+}
+
+template <typename TOut, int G>
+cudaError_t launch_tma_g(const FusedLaunch& L, const CUtensorMap& map, int nslots, cudaStream_t s) {
+    const size_t smem = ((size_t)(1 << (2 * G)) * fused_ws<G>() + K) * 4 + 128;
+    auto kern = planes_fused_tma<TOut, G>;
+    static unsigned long long attr_done = 0;  // per instantiation, one bit per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 64 || !((attr_done >> dev) & 1ull)) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev < 64) attr_done |= 1ull << dev;
+    }
+    dim3 grid((unsigned)L.ctas, (unsigned)nslots);
+    kern<<<grid, 32 * fused_warps<G>(), smem, s>>>(L, map);
+    return cudaGetLastError();
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime.
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (EncodeTiledFn) nullptr;
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
 // Shared-memory element type: 16 bits when the phase-1 results provably fit
 // (first pass of a uint8 volume: sums of at most 2^G <= 16 voxels of 255).
 template <typename TIn, typename TOut, typename T, bool INGEST>
@@ -105,6 +154,33 @@ cudaError_t launch_planes_fused(const FusedLaunch& L, int G, ElemKind in_kind, E
     if (in_kind == ElemKind::I32) {
         return out_kind == ElemKind::U16 ? cudaErrorInvalidValue
                                          : launch_fused_t<uint32_t, uint32_t, uint32_t, false>(L, G, nslots, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+bool fused_uses_tma(int G, ElemKind in_kind, bool ingest) {
+    return !ingest && in_kind == ElemKind::U16 && G >= 3;
+}
+
+cudaError_t launch_planes_fused_tma(const FusedLaunch& L, int G, ElemKind out_kind, const void* in_base,
+                                    size_t slot_stride, int nslots, cudaStream_t s) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    // 3-D view of the slots' input rows: x = displacement - base (the stored
+    // width), y = row, z = slot.  Elements outside it read as zero.
+    const cuuint64_t dims[3] = {(cuuint64_t)(L.dmax - L.gin.base), (cuuint64_t)L.N * L.N, (cuuint64_t)nslots};
+    const cuuint64_t strides[2] = {(cuuint64_t)L.gin.pitch * 2, (cuuint64_t)slot_stride};
+    const cuuint32_t box[3] = {(cuuint32_t)kStageElems, 1, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUtensorMap map;
+    const CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<void*>(in_base), dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    const bool to16 = out_kind == ElemKind::U16;
+    switch (G) {
+    case 3: return to16 ? launch_tma_g<uint16_t, 3>(L, map, nslots, s) : launch_tma_g<uint32_t, 3>(L, map, nslots, s);
+    case 4: return to16 ? launch_tma_g<uint16_t, 4>(L, map, nslots, s) : launch_tma_g<uint32_t, 4>(L, map, nslots, s);
     }
     return cudaErrorInvalidValue;
 }

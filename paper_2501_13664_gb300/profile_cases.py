@@ -1,0 +1,96 @@
+"""Small fixed workloads for profiling one kernel family at a time.
+
+    python -m paper_2501_13664_gb300.profile_cases CASE [--reps R] [--schedule 4,4]
+
+Each case builds its inputs with the seeded generators of ``synth``, runs the
+transform ``reps`` times on the current stream, synchronises, checks the
+device status word and prints one line.  The cases are sized for kernel
+profilers: inputs larger than the 129 MB L2 where the kernel streams, a few GB
+on the device at most.
+
+    fused-n256-d1   N=256 uint8 volume (1% sparse + 8 digital planes of 255),
+                    forward DRT of planes of dodecant 0 (both fused passes)
+    fused-n256      the same volume, all 12 dodecants (2.4 GB of int32 out)
+    inverse-n256    forward of dodecant 0, then its exact inverse
+    lines-n64-s0    N=64 int16 volume (uniform 0..1023 + 32 lines), DJT of
+                    sector 0 (268 MB of int32 out)
+    batched-c4-n64  80 uint8 volumes with the N <= 64 sizes of the 96-volume
+                    mixed batch, one persistent launch after one memset
+"""
+from __future__ import annotations
+
+import argparse
+
+import torch
+
+
+def _sched(s: str):
+    return tuple(int(x) for x in s.split(",")) if s else None
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("case", choices=["fused-n256-d1", "fused-n256", "inverse-n256", "lines-n64-s0", "batched-c4-n64"])
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--schedule", type=str, default="4,4", help="stage-fusion split of the N=256 planes cases")
+    args = ap.parse_args(argv)
+
+    import synth
+
+    from . import ALL, BatchPlan, get_plan, lines_forward, planes_forward, planes_inverse
+
+    dev = torch.device("cuda", 0)
+    sched = _sched(args.schedule)
+    status = 0
+    if args.case.startswith("fused") or args.case == "inverse-n256":
+        N = 256
+        vol = torch.from_numpy(synth.c2_volume(N)).to(dev)
+        plan = get_plan(N, torch.uint8)
+        if sched:
+            plan.set_schedule(sched)
+        mask = ALL if args.case == "fused-n256" else 1
+        out = torch.empty((bin(mask).count("1"), N, N, 3 * N), dtype=torch.int32, device=dev)
+        ws = plan.workspace("planes_forward")
+        if args.case == "inverse-n256":
+            planes_forward(vol, mask, out=out, workspace=ws)
+            iplan = get_plan(N, torch.int32)
+            iws = iplan.workspace("planes_inverse")
+            f = torch.empty((N, N, N), dtype=torch.int32, device=dev)
+            for _ in range(args.reps):
+                planes_inverse(out[0], 0, out=f, workspace=iws, check=False)
+            torch.cuda.synchronize()
+            status = iplan.device_error()
+            ok = bool(torch.equal(f, vol.to(torch.int32)))
+            print(f"{args.case}: reps={args.reps} status={status} round_trip_equal={ok}")
+            return 0 if (status == 0 and ok) else 1
+        for _ in range(args.reps):
+            planes_forward(vol, mask, out=out, workspace=ws)
+        torch.cuda.synchronize()
+        status = plan.device_error()
+        print(f"{args.case}: reps={args.reps} schedule={plan.schedule()} status={status} sum={int(out[0].sum())}")
+    elif args.case == "lines-n64-s0":
+        N = 64
+        vol = torch.from_numpy(synth.c3_volume(N)).to(dev)
+        plan = get_plan(N, torch.int16)
+        out = torch.empty((1, N, N, 2 * N, 2 * N), dtype=torch.int32, device=dev)
+        ws = plan.workspace("lines_forward")
+        for _ in range(args.reps):
+            lines_forward(vol, [0], out=out, workspace=ws)
+        torch.cuda.synchronize()
+        status = plan.device_error()
+        print(f"{args.case}: reps={args.reps} status={status} sum={int(out[0].sum())}")
+    else:
+        sizes = [N for N in synth.c4_sizes() if N <= 64]
+        vols = [torch.from_numpy(v).to(dev) for v in synth.c4_batch(sizes=sizes)]
+        bp = BatchPlan(sizes)
+        bp.bind(vols)
+        for _ in range(args.reps):
+            bp.run()
+        torch.cuda.synchronize()
+        status = bp.device_error()
+        print(f"{args.case}: reps={args.reps} volumes={len(sizes)} status={status}")
+    return 0 if status == 0 else 1
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
