@@ -122,6 +122,10 @@ drt3d_status drt3d_workspace_bytes(const drt3d_plan* plan, int op, size_t* bytes
  *   dodecant_mask : bit k selects dodecant k (1..0xFFF).
  *   d_ws, ws_bytes: workspace, >= drt3d_workspace_bytes(PLANES_FORWARD).
  * Integer results are exact (wrapping int32); F32 results are rounded sums.
+ * Passes over 16-bit intermediates stage their rows in shared memory with
+ * TMA loads whose completion is awaited for at most 0.2 s; a load still
+ * outstanding then leaves the output undefined and records DRT3D_ERR_TIMEOUT
+ * in the device status word (drt3d_get_device_error).
  * Errors: INVALID_ARG, ALIGN, WORKSPACE, CUDA. */
 drt3d_status drt3d_planes_forward(const drt3d_plan* plan, const void* d_in, void* d_out,
                                   uint32_t dodecant_mask, void* d_ws, size_t ws_bytes,

@@ -398,15 +398,24 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
                 if (!tma::mbar_wait(&mbar[u2], 0, kTmaWaitNs)) {
                     if (lane == 0 && L.status) atomicCAS(L.status, 0, (int)DRT3D_ERR_TIMEOUT);
                 }
+                // Two 8-byte reads per row from the 4-aligned element below the
+                // window; the in-chunk offset repeats with u1 mod 4 (as for the
+                // register path) and is unpacked at a compile-time offset.
                 const uint16_t* st = reinterpret_cast<const uint16_t*>(smem_raw + (size_t)u2 * R * WS * sizeof(TS));
                 const int g_lo = d0 + sg2 * u2;
+                Chunks16 w[R];
 #pragma unroll
                 for (int u1 = 0; u1 < R; ++u1) {
-                    const uint16_t* src = st + u1 * (kStageRowBytes / 2) + ((g_lo + sg1 * u1) & 7) + lane * K;
-#pragma unroll
-                    for (int i = 0; i < K; ++i) v[u1][i] = to_acc<uint16_t, T>(src[i]);
+                    const uint16_t* src = st + u1 * (kStageRowBytes / 2) + ((g_lo + sg1 * u1) & 4) + lane * K;
+                    w[u1].c[0] = *reinterpret_cast<const uint2*>(src);
+                    w[u1].c[1] = *reinterpret_cast<const uint2*>(src + 4);
                 }
                 __syncwarp();  // the group's results overwrite its staging
+                const int a = sg1 & 3, c = g_lo & 3;
+                unpack_class_u16<0, G>(c, w, v);
+                if constexpr (R > 1) unpack_class_u16<1, G>((c + a) & 3, w, v);
+                if constexpr (R > 2) unpack_class_u16<2, G>((c + 2 * a) & 3, w, v);
+                if constexpr (R > 3) unpack_class_u16<3, G>((c + 3 * a) & 3, w, v);
             } else if constexpr (sizeof(TIn) == 2) {
                 const int L0 = start - L.gin.base;  // window offset of row u1 = 0
                 const int width = L.dmax - L.gin.base;

@@ -16,119 +16,209 @@
 //
 // One CTA undoes a group of G half-stages along one axis for one unit: the
 // unit's 2^G rows over the whole stored displacement range sit in shared
-// memory, each of the 2^(G-1) pairs of a stage is one warp, and the suffix
-// sum of a segment of up to 1024 displacements is a register suffix sum over
-// each lane's contiguous chunk plus one warp shuffle scan of the chunk totals.
-// Recovered pairs overwrite the slots of the rows they came from.
+// memory for the whole group, and each of the 2^(G-1) pairs of a stage is one
+// warp.  A lane holds a CH-displacement chunk of both rows of its pair in
+// registers (CH = 8..32, chosen so that one warp's chunks cover a row), forms
+// nD = out_0 - out_1 and the chunk's suffix sums; one warp shuffle scan of the
+// chunk totals turns them into nT = -T.  lo = out_0 - nT
+// goes back over out_0 and nT over out_1; hi[e] = nT[e - S] is then a shifted
+// copy of that row, read as 16-byte vectors at a warp-uniform misalignment
+// and written in place (all reads of a segment before its writes).
+//
+// Shared layout: a row slot holds P prefix chunks (displacements below the
+// stored range, which the shifted copy reads) and NC chunks of CH words.
+// Chunks are CH + 4 words apart, and (CH/4 + 1) is odd: vector k of chunk c
+// then falls in 16-byte bank group (c (CH/4 + 1) + k) mod 8, so the three
+// access patterns -- lane = chunk, lane = consecutive vector, lane = chunk at
+// a common shifted offset -- each touch 8 distinct groups per quarter warp,
+// and a lane's vectors of one chunk sit at fixed offsets from its start.  Lanes whose chunk lies past the row
+// take part in the shuffle scans only: they read the last chunk's addresses
+// (served by broadcast, no extra traffic) and store nothing.
 #include "internal.cuh"
 
 namespace drt3d {
 namespace {
 
-constexpr int kInvWarps = 8;
+__host__ __device__ constexpr int inv_warps(int G) { return G >= 4 ? 8 : (1 << (G - 1)); }
+
+// Chunk width: the smallest of 8, 16, 24, 32 whose warp of chunks covers a
+// row of W displacements (32 beyond 1024: several segments).
+__host__ __device__ inline int inv_chunk_width(int W) { return W <= 256 ? 8 : W <= 512 ? 16 : W <= 768 ? 24 : 32; }
+
+// Prefix chunks of a slot: the shifted copy of a half-stage with slope so
+// far S reads down to displacement -(S + 3); S < 2^(m0 + G - 1).
+__host__ __device__ inline int inv_pre_chunks(int m0, int G, int CH) { return ((1 << (m0 + G - 1)) + 2 + CH - 1) / CH; }
+
+__host__ __device__ inline int inv_slot_words(int W, int m0, int G, int CH) {
+    return (inv_pre_chunks(m0, G, CH) + (W + CH - 1) / CH) * (CH + 4) + 4;
+}
 
 __device__ __forceinline__ void flag(int* status, int code) {
     if (*status == 0) atomicCAS(status, 0, code);
 }
 
-// Shared rows are stored in chunks of 32 displacements with one pad word per
-// chunk: element i of a row sits at (i / 32) * 33 + i % 32.  Lane L owns
-// chunk L during a scan, so "element k of every lane's chunk" falls on 32
-// distinct banks, and the lane-consecutive element i = lane + 32 * c used for
-// copies lands on consecutive words of chunk c.
-constexpr int kCh = 32;
-constexpr int kCs = 33;
-constexpr int kMaxChunks = 32;  // rows of up to 1024 displacements per segment
+// Word offset, within a slot, of element i (i >= -CH P).
+template <int CH>
+__device__ __forceinline__ int word_off(int i, int P) {
+    const int j = i + P * CH;  // >= 0
+    const int c = j / CH;
+    return c * (CH + 4) + (j - c * CH);
+}
 
-// T is stored with a prefix of kPre chunks below index 0 holding the values
-// hi reads there: T[0] for displacements >= 0, 0 below (kPre * 32 >= the
-// largest slope-so-far S of any half-stage, N/2 - 1 <= 511).
-constexpr int kPre = 16;
+__device__ __forceinline__ uint4 lds4(const uint32_t* s, int off) { return *reinterpret_cast<const uint4*>(s + off); }
+__device__ __forceinline__ void sts4(uint32_t* s, int off, uint4 v) { *reinterpret_cast<uint4*>(s + off) = v; }
 
-template <int G>
-__global__ void __launch_bounds__(kInvWarps * 32, 2)
+// hi[e] = nT[e - S] over a pair's hi row, in place over nT (slot s1), for
+// one compile-time in-vector misalignment RR = (-S) & 3.  Segments go from
+// the top; inside one, every lane reads its whole window before any lane
+// writes.  Lanes past the row read the last chunk's window (broadcast) and
+// store nothing.
+template <int CH, int RR>
+__device__ __forceinline__ void hi_pass(uint32_t* s1, int S, int P, int NC, int W, int lane) {
+    constexpr int VPC = CH / 4;               // vectors per chunk
+    constexpr int NVEC = RR ? VPC + 1 : VPC;  // vectors covering the window
+    const int nseg = (NC + 31) / 32;
+#pragma unroll 1
+    for (int sgm = nseg - 1; sgm >= 0; --sgm) {
+        const int c = sgm * 32 + lane;
+        const int ce = c < NC ? c : NC - 1;
+        const int pa = CH * ce - S - RR;  // aligned window start (element)
+        const int w0 = word_off<CH>(pa, P);
+        const int kb = VPC - (((pa + P * CH) % CH) >> 2);  // vectors before the next chunk starts
+        uint32_t src[4 * NVEC];
+#pragma unroll
+        for (int t = 0; t < NVEC; ++t) {
+            const uint4 w = lds4(s1, w0 + 4 * t + (t >= kb ? 4 : 0));
+            src[4 * t] = w.x; src[4 * t + 1] = w.y; src[4 * t + 2] = w.z; src[4 * t + 3] = w.w;
+        }
+        __syncwarp();
+        uint32_t* dst = s1 + (c + P) * (CH + 4);
+        const int past = W - CH * c;  // elements of this chunk inside the stored width
+        if (past >= CH) {
+#pragma unroll
+            for (int kv = 0; kv < VPC; ++kv)
+                sts4(dst, 4 * kv,
+                     make_uint4(src[4 * kv + RR], src[4 * kv + 1 + RR], src[4 * kv + 2 + RR], src[4 * kv + 3 + RR]));
+        } else if (past > 0) {
+#pragma unroll
+            for (int k = 0; k < CH; ++k) dst[k] = k < past ? src[k + RR] : 0u;
+        }
+        __syncwarp();
+    }
+}
+
+template <int G, int CH>
+__global__ void __launch_bounds__(inv_warps(G) * 32, (G >= 4 ? 2 : 4))
 planes_inv_pass(const __grid_constant__ InvLaunch L) {
     constexpr int R = 1 << G;
-    constexpr int PAIRS = R / 2;
+    constexpr int NW = inv_warps(G);
+    constexpr int NT = NW * 32;
+    constexpr int VPC = CH / 4;
+    constexpr int RUN = CH / 4;  // suffix-sum run length (4 runs per chunk)
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int W = L.dmax - L.gin.base;   // stored row length of the input geometry
-    const int NC = (W + kCh - 1) / kCh;  // chunks per row
-    const int WS = NC * kCs;
-    const int TS = (NC + kPre) * kCs;    // per-pair T buffer with its prefix
-    uint32_t* rows = reinterpret_cast<uint32_t*>(smem_raw);  // [R][WS]
-    uint32_t* scan = rows + R * WS;                          // [PAIRS][TS]
+    uint32_t* rows = reinterpret_cast<uint32_t*>(smem_raw);
     __shared__ int slot[R];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = L.N, m0 = L.m0;
+    const int base = L.gin.base;
+    const int W = L.dmax - base;       // stored row length of the input geometry
+    const int NC = (W + CH - 1) / CH;  // chunks per row
+    const int P = inv_pre_chunks(m0, G, CH);
+    const int RS = inv_slot_words(W, m0, G, CH);
     unsigned unit = blockIdx.x;
     const int sg = (int)(unit & ((1u << m0) - 1)); unit >>= m0;
     const int wb = L.n - m0 - G;
     const int wq = (int)(unit & ((1u << wb) - 1));
     const int j = (int)(unit >> wb);
-    const long long rs_axis = L.axis == 0 ? N : 1;   // row stride of the undone axis
+    const long long rs_axis = L.axis == 0 ? N : 1;  // row stride of the undone axis
     const long long rs_other = L.axis == 0 ? 1 : N;
 
-    // Load the unit's output rows o(t) = t + (sg << G) + (w << (m0 + G)),
-    // zero-padding the last chunk.
-    const uint32_t* in = static_cast<const uint32_t*>(L.in);
-    for (int t = warp; t < R; t += kInvWarps) {
-        const long long row = (long long)(t + (sg << G) + (wq << (m0 + G))) * rs_axis + (long long)j * rs_other;
-        const uint32_t* src = in + row * L.gin.pitch + lane;
-        uint32_t* dst = rows + t * WS + lane;
-        for (int c0 = 0; c0 < NC; c0 += 16) {
-            uint32_t v[16];
+    // ---- load the unit's output rows o(t) = t + (sg << G) + (w << (m0 + G)),
+    // zeros past the stored width in the last chunk
+    {
+        const uint32_t* in = static_cast<const uint32_t*>(L.in);
+        const bool vec_in = (L.gin.pitch & 3) == 0;
+        const int NV = NC * VPC;  // 16-byte vectors per row
+        constexpr int B = 8;      // vectors in flight per lane
+        for (int t = warp; t < R; t += NW) {
+            const long long row = (long long)(t + (sg << G) + (wq << (m0 + G))) * rs_axis + (long long)j * rs_other;
+            const uint32_t* src = in + row * L.gin.pitch;
+            uint32_t* dst = rows + t * RS;
+            for (int v0 = lane; v0 < NV; v0 += B * 32) {
+                uint4 w[B];
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
-                v[c] = (c0 + c) * kCh + lane < W ? __ldg(src + (c0 + c) * kCh) : 0u;
+                for (int b = 0; b < B; ++b) {
+                    const int i = 4 * (v0 + 32 * b);
+                    w[b] = make_uint4(0u, 0u, 0u, 0u);
+                    if (vec_in && i + 4 <= W) {
+                        w[b] = __ldg(reinterpret_cast<const uint4*>(src + i));
+                    } else if (i < W) {
+                        w[b].x = __ldg(src + i);
+                        if (i + 1 < W) w[b].y = __ldg(src + i + 1);
+                        if (i + 2 < W) w[b].z = __ldg(src + i + 2);
+                        if (i + 3 < W) w[b].w = __ldg(src + i + 3);
+                    }
+                }
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
-                if (c0 + c < NC) dst[(c0 + c) * kCs] = v[c];
+                for (int b = 0; b < B; ++b)
+                    if (v0 + 32 * b < NV) sts4(dst, word_off<CH>(4 * (v0 + 32 * b), P), w[b]);
+            }
         }
     }
     if (threadIdx.x < R) slot[threadIdx.x] = threadIdx.x;
     __syncthreads();
 
-    const int base = L.gin.base;
-    const int top = L.dmax;  // 3N
-    // Rows whose length is a whole number of chunks need no masking at all.
-    const bool whole = (W & (kCh - 1)) == 0;
+    const int nseg = (NC + 31) / 32;
 #pragma unroll 1
     for (int J = G - 1; J >= 0; --J) {
         const int half = 1 << J;
-        if (warp < PAIRS) {
-            const int q = warp >> J, tau = warp & (half - 1);
-            const int r0 = 2 * tau + (q << (J + 1));      // rows of stage J+1 (within the unit)
-            const int S = (sg << J) + tau;                 // slope so far at global stage m0 + J
-            uint32_t* o0 = rows + slot[r0] * WS;
-            uint32_t* o1 = rows + slot[r0 + 1] * WS;
-            uint32_t* T = scan + warp * TS + kPre * kCs;   // T[0] after the prefix
-            const int lim = top - 1 - S - base;            // last stored index with a free Delta
-            // Data in the range has Delta = 0 past lim; check it there (the
-            // scan below does not mask it: for such data masking changes
-            // nothing, and other data is reported and left undefined).
-            bool bad = false;
-            for (int i = lim + 1 + lane; i < W; i += 32) bad |= o1[(i >> 5) * kCs + (i & 31)] != o0[(i >> 5) * kCs + (i & 31)];
-            if (__any_sync(0xffffffffu, bad) && lane == 0) flag(L.status, DRT3D_ERR_NOT_IN_RANGE);
-            uint32_t seg_carry = 0;
-            // Segments of kMaxChunks chunks from the top; lane L owns chunk
-            // seg * 32 + L of the segment.
-            const int nseg = (NC + kMaxChunks - 1) / kMaxChunks;
+        {
+            const int p = warp;  // one pair per warp
+            const int q = p >> J, tau = p & (half - 1);
+            const int r0 = 2 * tau + (q << (J + 1));  // rows of stage J+1 (within the unit)
+            const int S = (sg << J) + tau;            // slope so far at global stage m0 + J
+            uint32_t* s0 = rows + slot[r0] * RS;
+            uint32_t* s1 = rows + slot[r0 + 1] * RS;
+
+            // Data in the range has Delta = 0 past 3N - 1 - S; check it there.
+            {
+                bool bad = false;
+                const int from = W - S > 0 ? W - S : 0;
+                for (int i = from + lane; i < W; i += 32)
+                    bad |= s0[word_off<CH>(i, P)] != s1[word_off<CH>(i, P)];
+                if (__any_sync(0xffffffffu, bad) && lane == 0) flag(L.status, DRT3D_ERR_NOT_IN_RANGE);
+            }
+
+            // nT = -(suffix sums of Delta); lo = out_0 - nT.  Segments of 32
+            // chunks from the top; lane L owns chunk 32 * seg + L.
+            uint32_t seg_carry = 0, first = 0;
 #pragma unroll 1
             for (int sgm = nseg - 1; sgm >= 0; --sgm) {
-                const int c = sgm * kMaxChunks + lane;
+                const int c = sgm * 32 + lane;
                 const bool live = c < NC;
-                uint32_t* p0 = o0 + (live ? c : 0) * kCs;
-                uint32_t* p1 = o1 + (live ? c : 0) * kCs;
-                uint32_t a[kCh], x[kCh];
+                const int cw = ((live ? c : NC - 1) + P) * (CH + 4);  // chunk start (words)
+                uint32_t a[CH], x[CH];
 #pragma unroll
-                for (int k = 0; k < kCh; ++k) {
-                    a[k] = p0[k];
-                    x[k] = live ? p1[k] - a[k] : 0u;
+                for (int kv = 0; kv < VPC; ++kv) {
+                    const uint4 A = lds4(s0, cw + 4 * kv);
+                    const uint4 Bv = lds4(s1, cw + 4 * kv);
+                    a[4 * kv] = A.x; a[4 * kv + 1] = A.y; a[4 * kv + 2] = A.z; a[4 * kv + 3] = A.w;
+                    x[4 * kv] = A.x - Bv.x; x[4 * kv + 1] = A.y - Bv.y;
+                    x[4 * kv + 2] = A.z - Bv.z; x[4 * kv + 3] = A.w - Bv.w;
                 }
+                // Chunk suffix sums as 4 independent runs (short dependency
+                // chains), then the runs' carries.
 #pragma unroll
-                for (int k = kCh - 2; k >= 0; --k) x[k] += x[k + 1];
-                const uint32_t tot = x[0];
+                for (int k = RUN - 2; k >= 0; --k)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) x[RUN * b + k] += x[RUN * b + k + 1];
+                uint32_t rc[4];
+                rc[3] = 0u;
+                rc[2] = x[3 * RUN];
+                rc[1] = rc[2] + x[2 * RUN];
+                rc[0] = rc[1] + x[RUN];
+                const uint32_t tot = live ? x[0] + rc[0] : 0u;
                 uint32_t y = tot;
 #pragma unroll
                 for (int off = 1; off < 32; off <<= 1) {
@@ -136,52 +226,50 @@ planes_inv_pass(const __grid_constant__ InvLaunch L) {
                     if (lane + off < 32) y += z;
                 }
                 const uint32_t carry = y - tot + seg_carry;
-                if (live) {
-                    uint32_t* pt = T + c * kCs;
 #pragma unroll
-                    for (int k = 0; k < kCh; ++k) {
-                        const uint32_t t = x[k] + carry;
-                        pt[k] = t;
-                        p0[k] = a[k] + t;  // lo[d] = out0[d] + T[d]
+                for (int b = 0; b < 4; ++b) rc[b] += carry;
+#pragma unroll
+                for (int k = 0; k < CH; ++k) {
+                    x[k] += rc[k / RUN];  // nT
+                    a[k] -= x[k];         // lo = out_0 + T
+                }
+                first = x[0];
+                if (live) {
+#pragma unroll
+                    for (int kv = 0; kv < VPC; ++kv) {
+                        sts4(s0, cw + 4 * kv, make_uint4(a[4 * kv], a[4 * kv + 1], a[4 * kv + 2], a[4 * kv + 3]));
+                        sts4(s1, cw + 4 * kv, make_uint4(x[4 * kv], x[4 * kv + 1], x[4 * kv + 2], x[4 * kv + 3]));
                     }
                 }
                 seg_carry += __shfl_sync(0xffffffffu, y, 0);
             }
-            __syncwarp();
-            // Prefix below T[0]: T is constant (= T[0]) below the stored range,
+            // Prefix below the stored range: T is constant (= T[0]) there,
             // where Delta vanishes, and hi is 0 below displacement 0.
-            const uint32_t T0 = T[0];
-            for (int jj = -(lane + 1); jj >= -S; jj -= 32)
-                T[(jj >> 5) * kCs + (jj & 31)] = (base + jj >= 0) ? T0 : 0u;
+            const uint32_t nT0 = __shfl_sync(0xffffffffu, first, 0);
+            for (int v = lane; v < VPC * P; v += 32) {
+                const int i = -CH * P + 4 * v;
+                const uint32_t f = base + i >= 0 ? nT0 : 0u;
+                sts4(s1, word_off<CH>(i, P), make_uint4(f, f, f, f));
+            }
             __syncwarp();
-            // hi[i] = -T[i - S]
-            for (int c = lane; c < NC; c += 32) {
-                const int i0 = c * kCh;
-                uint32_t* p1 = o1 + c * kCs;
-                const int jb = i0 - S;  // source index of element 0 (>= -S)
-                const int rb = jb & 31;
-                const uint32_t* ps = T + (jb >> 5) * kCs + rb;  // element k: next chunk once rb + k >= 32
-                if (whole || i0 + kCh <= W) {
-#pragma unroll
-                    for (int k = 0; k < kCh; ++k) p1[k] = 0u - ps[k + (k >= 32 - rb ? 1 : 0)];
-                } else {
-#pragma unroll
-                    for (int k = 0; k < kCh; ++k)
-                        if (i0 + k < W) p1[k] = 0u - ps[k + (k >= 32 - rb ? 1 : 0)];
-                }
+            // hi[e] = nT[e - S], in place over nT.
+            switch ((-S) & 3) {
+            case 0: hi_pass<CH, 0>(s1, S, P, NC, W, lane); break;
+            case 1: hi_pass<CH, 1>(s1, S, P, NC, W, lane); break;
+            case 2: hi_pass<CH, 2>(s1, S, P, NC, W, lane); break;
+            default: hi_pass<CH, 3>(s1, S, P, NC, W, lane); break;
             }
         }
         __syncthreads();
         if (threadIdx.x < 32) {
-            // new slot of every row of stage J (computed by one warp, lane r)
+            // new slot of every row of stage J (lane r)
             const int r = threadIdx.x;
             int ns = 0;
             if (r < R) {
-                const int hi = (r >> J) & 1;        // position bit J of the stage-J row
-                const int a = r - (hi << J);        // its lo partner
+                const int hb = (r >> J) & 1;   // position bit J of the stage-J row
+                const int a = r - (hb << J);   // its lo partner
                 const int q = a >> (J + 1), tau = a & (half - 1);
-                const int r0 = 2 * tau + (q << (J + 1));
-                ns = slot[r0 + hi];
+                ns = slot[2 * tau + (q << (J + 1)) + hb];
             }
             __syncwarp();
             if (r < R) slot[r] = ns;
@@ -189,65 +277,136 @@ planes_inv_pass(const __grid_constant__ InvLaunch L) {
         __syncthreads();
     }
 
-    // Store the unit's input rows a(u) = sg + (u << m0) + (w << (m0 + G)).
+    // ---- store the unit's input rows a(u) = sg + (u << m0) + (w << (m0 + G)).
     // Recovered values below the output geometry's lower bound must vanish.
-    const int lo_out = L.lo_out;
-    for (int u = warp; u < R; u += kInvWarps) {
-        const int a = sg + (u << m0) + (wq << (m0 + G));
-        const uint32_t* srow = rows + slot[u] * WS + lane;
-        bool bad = false;
-        if (L.scatter) {
-            // Stage 0 rows: the volume sits at d in [2N, 3N) of the frame row (x', y').
-            const int xp = L.axis == 0 ? a : j, yp = L.axis == 0 ? j : a;
-            int32_t* vol = static_cast<int32_t*>(L.out);
-            const long long rb = L.map.o0 + xp * L.map.sx + yp * L.map.sy;
-            for (int c = 0; c < NC; ++c) {
-                const int i = c * kCh + lane;
-                if (i >= W) break;
-                const int d = base + i;
-                const uint32_t v = srow[c * kCs];
-                if (d < 2 * N) bad |= v != 0u;
-                else vol[rb + (long long)(d - 2 * N) * L.map.sz] = (int32_t)v;
-            }
-        } else {
+    bool bad = false;
+    if (!L.scatter) {
+        const int lo_out = L.lo_out;
+        const bool vec_out = (L.gout.pitch & 3) == 0;
+        uint32_t* out = static_cast<uint32_t*>(L.out);
+        for (int u = warp; u < R; u += NW) {
+            const int a = sg + (u << m0) + (wq << (m0 + G));
             const long long row = (long long)a * rs_axis + (long long)j * rs_other;
-            uint32_t* dst = static_cast<uint32_t*>(L.out) + row * L.gout.pitch - L.gout.base + base + lane;
-            for (int c = 0; c < NC; ++c) {
-                const int i = c * kCh + lane;
-                if (i >= W) break;
+            uint32_t* dst = out + row * L.gout.pitch - L.gout.base + base;  // element i of the stored row
+            const uint32_t* srow = rows + slot[u] * RS;
+            for (int v = lane; 4 * v < W; v += 32) {
+                const int i = 4 * v;
                 const int d = base + i;
-                const uint32_t v = srow[c * kCs];
-                if (d < lo_out) bad |= v != 0u;
-                if (d >= L.gout.base) dst[c * kCh] = v;
+                const uint4 w = lds4(srow, word_off<CH>(i, P));
+                const uint32_t e[4] = {w.x, w.y, w.z, w.w};
+                if (d < lo_out) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (d + k < lo_out) bad |= e[k] != 0u;
+                }
+                if (d >= L.gout.base) {
+                    if (vec_out && i + 4 <= W) {
+                        *reinterpret_cast<uint4*>(dst + i) = w;
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if (i + k < W) dst[i + k] = e[k];
+                    }
+                }
             }
         }
-        if (__any_sync(0xffffffffu, bad) && lane == 0) flag(L.status, DRT3D_ERR_NOT_IN_RANGE);
+    } else {
+        // Stage-0 rows: the volume sits at d in [2N, 3N) of frame row (x', y').
+        int32_t* vol = static_cast<int32_t*>(L.out);
+        const Affine& M = L.map;
+        const long long s_row = L.axis == 0 ? M.sx : M.sy;  // volume stride between rows u, u + 1
+        if (M.sz == 1 || (s_row != 1 && s_row != -1)) {
+            // lanes along d
+            for (int u = warp; u < R; u += NW) {
+                const int a = sg + (u << m0) + (wq << (m0 + G));
+                const int xp = L.axis == 0 ? a : j, yp = L.axis == 0 ? j : a;
+                const long long rb = M.o0 + xp * M.sx + yp * M.sy;
+                const uint32_t* srow = rows + slot[u] * RS;
+                for (int v = lane; 4 * v < W; v += 32) {
+                    const int i = 4 * v;
+                    const int d = base + i;
+                    const uint4 w = lds4(srow, word_off<CH>(i, P));
+                    const uint32_t e[4] = {w.x, w.y, w.z, w.w};
+                    if (M.sz == 1 && d >= 2 * N && i + 4 <= W && ((rb + d - 2 * N) & 3) == 0) {
+                        *reinterpret_cast<uint4*>(vol + rb + (d - 2 * N)) = w;
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            if (i + k >= W) break;
+                            if (d + k < 2 * N) bad |= e[k] != 0u;
+                            else vol[rb + (long long)(d + k - 2 * N) * M.sz] = (int32_t)e[k];
+                        }
+                    }
+                }
+            }
+        } else {
+            // lanes along the rows u (unit stride in the volume)
+            for (int idx = threadIdx.x; idx < R * W; idx += NT) {
+                const int i = idx / R, u = idx - i * R;
+                const int d = base + i;
+                const uint32_t e = rows[slot[u] * RS + word_off<CH>(i, P)];
+                if (d < 2 * N) {
+                    bad |= e != 0u;
+                } else {
+                    const int a = sg + (u << m0) + (wq << (m0 + G));
+                    const int xp = L.axis == 0 ? a : j, yp = L.axis == 0 ? j : a;
+                    vol[M.o0 + xp * M.sx + yp * M.sy + (long long)(d - 2 * N) * M.sz] = (int32_t)e;
+                }
+            }
+        }
     }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) flag(L.status, DRT3D_ERR_NOT_IN_RANGE);
 }
 
-size_t inv_smem(int G, int W) {
-    const int NC = (W + kCh - 1) / kCh;
-    return ((size_t)(1 << G) * NC + (size_t)((1 << G) / 2) * (NC + kPre)) * kCs * 4;
+size_t inv_smem(int G, int W, int m0) {
+    return (size_t)(1 << G) * inv_slot_words(W, m0, G, inv_chunk_width(W)) * 4;
+}
+
+template <int G, int CH>
+cudaError_t launch_inv_gc(const InvLaunch& L, cudaStream_t s) {
+    const int W = L.dmax - L.gin.base;
+    const size_t smem = inv_smem(G, W, L.m0);
+    auto kern = planes_inv_pass<G, CH>;
+    // The size cap is per device: raise it once to the device's opt-in
+    // maximum (occupancy follows the size each launch asks for).
+    static unsigned long long attr_done = 0;  // one bit per device
+    static int optin_max[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64) return cudaErrorInvalidDevice;
+    if (!((attr_done >> dev) & 1ull)) {
+        int mx = 0;
+        e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return e;
+        cudaFuncAttributes fa{};
+        e = cudaFuncGetAttributes(&fa, kern);
+        if (e != cudaSuccess) return e;
+        mx -= (int)fa.sharedSizeBytes;  // the cap counts dynamic memory only, beside the static
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        if (e != cudaSuccess) return e;
+        optin_max[dev] = mx;
+        attr_done |= 1ull << dev;
+    }
+    if (smem > (size_t)optin_max[dev]) return cudaErrorInvalidValue;
+    const unsigned units = (unsigned)((long long)L.N << (L.n - G));
+    kern<<<units, inv_warps(G) * 32, smem, s>>>(L);
+    return cudaGetLastError();
 }
 
 template <int G>
 cudaError_t launch_inv_g(const InvLaunch& L, cudaStream_t s) {
-    const int W = L.dmax - L.gin.base;
-    const size_t smem = inv_smem(G, W);
-    auto kern = planes_inv_pass<G>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const unsigned units = (unsigned)((long long)L.N << (L.n - G));
-    kern<<<units, kInvWarps * 32, smem, s>>>(L);
-    return cudaGetLastError();
+    switch (inv_chunk_width(L.dmax - L.gin.base)) {
+    case 8: return launch_inv_gc<G, 8>(L, s);
+    case 16: return launch_inv_gc<G, 16>(L, s);
+    case 24: return launch_inv_gc<G, 24>(L, s);
+    default: return launch_inv_gc<G, 32>(L, s);
+    }
 }
 
 }  // namespace
 
-size_t inverse_smem_bytes(int N, int G, int base) {
-    const int W = 3 * N - base;
-    return inv_smem(G, W);
-}
+size_t inverse_smem_bytes(int N, int G, int base, int m0) { return inv_smem(G, 3 * N - base, m0); }
 
 cudaError_t launch_planes_inverse_pass(const InvLaunch& L, int G, cudaStream_t s) {
     switch (G) {
