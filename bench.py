@@ -148,15 +148,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_hash() -> str:
-    """sha256 of the CUDA sources (a stored ncu traffic figure is only valid for them)."""
-    import glob
+def kernel_source_hash(files) -> str:
+    """sha256 over the named CUDA sources (under the package's csrc/): a stored
+    ncu traffic figure is valid only for the sources it was taken on."""
     import hashlib
 
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2501_13664_gb300", "csrc", "*"))):
-        with open(p, "rb") as f:
-            h.update(os.path.basename(p).encode() + b"\0" + f.read())
+    for name in sorted(files):
+        with open(os.path.join(ROOT, "paper_2501_13664_gb300", "csrc", name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()
 
 
@@ -166,13 +166,12 @@ def ncu_traffic(kernel: str):
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(p) as f:
-            d = json.load(f)
-    except (OSError, ValueError):
+            e = json.load(f).get("kernels", {}).get(kernel)
+        if e is None or e.get("source_sha256") != kernel_source_hash(e["sources"]):
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
         return None
-    if d.get("source_sha256") != kernel_source_hash():
-        return None
-    e = d.get("kernels", {}).get(kernel)
-    return None if e is None else float(e["dram_bytes_per_launch"])
 
 
 def measured_peaks() -> dict:
