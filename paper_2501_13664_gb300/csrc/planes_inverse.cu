@@ -73,11 +73,11 @@ __device__ __forceinline__ void sts4(uint32_t* s, int off, uint4 v) { *reinterpr
 // the top; inside one, every lane reads its whole window before any lane
 // writes.  Lanes past the row read the last chunk's window (broadcast) and
 // store nothing.
-template <int CH, int RR>
+template <int CH, int RR, bool MULTI>
 __device__ __forceinline__ void hi_pass(uint32_t* s1, int S, int P, int NC, int W, int lane) {
     constexpr int VPC = CH / 4;               // vectors per chunk
     constexpr int NVEC = RR ? VPC + 1 : VPC;  // vectors covering the window
-    const int nseg = (NC + 31) / 32;
+    const int nseg = MULTI ? (NC + 31) / 32 : 1;
 #pragma unroll 1
     for (int sgm = nseg - 1; sgm >= 0; --sgm) {
         const int c = sgm * 32 + lane;
@@ -107,7 +107,9 @@ __device__ __forceinline__ void hi_pass(uint32_t* s1, int S, int P, int NC, int 
     }
 }
 
-template <int G, int CH>
+// MULTI: rows of more than 32 chunks, scanned in segments of 32 chunks from
+// the top with a carry; otherwise one segment.
+template <int G, int CH, bool MULTI>
 __global__ void __launch_bounds__(inv_warps(G) * 32, (G >= 4 ? 2 : 4))
 planes_inv_pass(const __grid_constant__ InvLaunch L) {
     constexpr int R = 1 << G;
@@ -169,7 +171,7 @@ planes_inv_pass(const __grid_constant__ InvLaunch L) {
     if (threadIdx.x < R) slot[threadIdx.x] = threadIdx.x;
     __syncthreads();
 
-    const int nseg = (NC + 31) / 32;
+    const int nseg = MULTI ? (NC + 31) / 32 : 1;
 #pragma unroll 1
     for (int J = G - 1; J >= 0; --J) {
         const int half = 1 << J;
@@ -185,7 +187,12 @@ planes_inv_pass(const __grid_constant__ InvLaunch L) {
             {
                 bool bad = false;
                 const int from = W - S > 0 ? W - S : 0;
-                for (int i = from + lane; i < W; i += 32)
+#pragma unroll
+                for (int it = 0; it < 4; ++it) {  // S < 128: at most 4 rounds
+                    const int i = from + lane + 32 * it;
+                    if (i < W) bad |= s0[word_off<CH>(i, P)] != s1[word_off<CH>(i, P)];
+                }
+                for (int i = from + 128 + lane; i < W; i += 32)
                     bad |= s0[word_off<CH>(i, P)] != s1[word_off<CH>(i, P)];
                 if (__any_sync(0xffffffffu, bad) && lane == 0) flag(L.status, DRT3D_ERR_NOT_IN_RANGE);
             }
@@ -246,7 +253,14 @@ planes_inv_pass(const __grid_constant__ InvLaunch L) {
             // Prefix below the stored range: T is constant (= T[0]) there,
             // where Delta vanishes, and hi is 0 below displacement 0.
             const uint32_t nT0 = __shfl_sync(0xffffffffu, first, 0);
-            for (int v = lane; v < VPC * P; v += 32) {
+#pragma unroll
+            for (int it = 0; it < 2; ++it) {
+                const int v = lane + 32 * it;
+                const int i = -CH * P + 4 * v;
+                const uint32_t f = base + i >= 0 ? nT0 : 0u;
+                if (v < VPC * P) sts4(s1, word_off<CH>(i, P), make_uint4(f, f, f, f));
+            }
+            for (int v = lane + 64; v < VPC * P; v += 32) {
                 const int i = -CH * P + 4 * v;
                 const uint32_t f = base + i >= 0 ? nT0 : 0u;
                 sts4(s1, word_off<CH>(i, P), make_uint4(f, f, f, f));
@@ -254,10 +268,10 @@ planes_inv_pass(const __grid_constant__ InvLaunch L) {
             __syncwarp();
             // hi[e] = nT[e - S], in place over nT.
             switch ((-S) & 3) {
-            case 0: hi_pass<CH, 0>(s1, S, P, NC, W, lane); break;
-            case 1: hi_pass<CH, 1>(s1, S, P, NC, W, lane); break;
-            case 2: hi_pass<CH, 2>(s1, S, P, NC, W, lane); break;
-            default: hi_pass<CH, 3>(s1, S, P, NC, W, lane); break;
+            case 0: hi_pass<CH, 0, MULTI>(s1, S, P, NC, W, lane); break;
+            case 1: hi_pass<CH, 1, MULTI>(s1, S, P, NC, W, lane); break;
+            case 2: hi_pass<CH, 2, MULTI>(s1, S, P, NC, W, lane); break;
+            default: hi_pass<CH, 3, MULTI>(s1, S, P, NC, W, lane); break;
             }
         }
         __syncthreads();
@@ -362,11 +376,11 @@ size_t inv_smem(int G, int W, int m0) {
     return (size_t)(1 << G) * inv_slot_words(W, m0, G, inv_chunk_width(W)) * 4;
 }
 
-template <int G, int CH>
+template <int G, int CH, bool MULTI>
 cudaError_t launch_inv_gc(const InvLaunch& L, cudaStream_t s) {
     const int W = L.dmax - L.gin.base;
     const size_t smem = inv_smem(G, W, L.m0);
-    auto kern = planes_inv_pass<G, CH>;
+    auto kern = planes_inv_pass<G, CH, MULTI>;
     // The size cap is per device: raise it once to the device's opt-in
     // maximum (occupancy follows the size each launch asks for).
     static unsigned long long attr_done = 0;  // one bit per device
@@ -396,11 +410,13 @@ cudaError_t launch_inv_gc(const InvLaunch& L, cudaStream_t s) {
 
 template <int G>
 cudaError_t launch_inv_g(const InvLaunch& L, cudaStream_t s) {
-    switch (inv_chunk_width(L.dmax - L.gin.base)) {
-    case 8: return launch_inv_gc<G, 8>(L, s);
-    case 16: return launch_inv_gc<G, 16>(L, s);
-    case 24: return launch_inv_gc<G, 24>(L, s);
-    default: return launch_inv_gc<G, 32>(L, s);
+    const int W = L.dmax - L.gin.base;
+    switch (inv_chunk_width(W)) {
+    case 8: return launch_inv_gc<G, 8, false>(L, s);
+    case 16: return launch_inv_gc<G, 16, false>(L, s);
+    case 24: return launch_inv_gc<G, 24, false>(L, s);
+    default:
+        return (W + 31) / 32 > 32 ? launch_inv_gc<G, 32, true>(L, s) : launch_inv_gc<G, 32, false>(L, s);
     }
 }
 
