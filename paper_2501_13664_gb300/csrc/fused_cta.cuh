@@ -503,5 +503,186 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
     }
 }
 
+// ---------------------------------------------------------------------------
+// First pass of a uint8 volume with two row groups per register.
+//
+// With G = 4 every phase-1 value is a sum of at most 16 voxels (<= 4080) and
+// every phase-2 value a sum of at most 256 (<= 65280): both fit 16 bits.  A
+// warp's two phase-1 groups (u2 = warp, warp + 8) see identical shifts (the
+// shear is applied by the loads, and it is zero at m0 = 0), and so do its two
+// phase-2 groups (t1 = warp, warp + 8).  So each 32-bit register carries one
+// value of each group, low and high half, and one 32-bit add adds both with no
+// carry between the halves: half the adds and shuffles of the plain path.
+
+// [A_e0, 0, B_e0, 0] and [A_e1, 0, B_e1, 0] from t = [A_e0, B_e0, A_e1, B_e1].
+__device__ __forceinline__ uint32_t spread_lo(uint32_t t) { return __byte_perm(t, 0u, 0x4140); }
+__device__ __forceinline__ uint32_t spread_hi(uint32_t t) { return __byte_perm(t, 0u, 0x4342); }
+
+template <typename TOut, int G>
+__device__ __forceinline__ void store_rows_x2(const FusedLaunch& L, const FusedSlot& sp,
+                                              const uint32_t (&v)[1 << G][K], int t1A, int t1B, int wq1, int wq2,
+                                              int rs1, int rs2, int d0, int lane) {
+    constexpr int R = 1 << G;
+    const int p0 = lane * K;
+    const int d = d0 + p0;
+    if (p0 >= L.V || d >= L.dmax) return;
+    // m0 = 0: slopes so far are zero
+    TOut* out = static_cast<TOut*>(sp.out) + (d - L.gout.base);
+    const long long colr = (long long)(wq2 << G) * rs2;
+    const long long rstride = (long long)rs2 * L.gout.pitch;
+    TOut* dA = out + ((long long)(t1A + (wq1 << G)) * rs1 + colr) * L.gout.pitch;
+    TOut* dB = out + ((long long)(t1B + (wq1 << G)) * rs1 + colr) * L.gout.pitch;
+    if (L.vec_store) {
+#pragma unroll
+        for (int t2 = 0; t2 < R; ++t2, dA += rstride, dB += rstride) {
+            if constexpr (sizeof(TOut) == 2) {
+                st_global(reinterpret_cast<uint2*>(dA), make_uint2(__byte_perm(v[t2][0], v[t2][1], 0x5410),
+                                                                   __byte_perm(v[t2][2], v[t2][3], 0x5410)));
+                st_global(reinterpret_cast<uint2*>(dB), make_uint2(__byte_perm(v[t2][0], v[t2][1], 0x7632),
+                                                                   __byte_perm(v[t2][2], v[t2][3], 0x7632)));
+            } else {
+                st_global(reinterpret_cast<uint4*>(dA), make_uint4(v[t2][0] & 0xFFFFu, v[t2][1] & 0xFFFFu,
+                                                                   v[t2][2] & 0xFFFFu, v[t2][3] & 0xFFFFu));
+                st_global(reinterpret_cast<uint4*>(dB), make_uint4(v[t2][0] >> 16, v[t2][1] >> 16, v[t2][2] >> 16,
+                                                                   v[t2][3] >> 16));
+            }
+        }
+    } else {
+#pragma unroll
+        for (int t2 = 0; t2 < R; ++t2, dA += rstride, dB += rstride)
+#pragma unroll
+            for (int i = 0; i < K; ++i)
+                if (d + i < L.dmax) {
+                    st_global(dA + i, (TOut)(v[t2][i] & 0xFFFFu));
+                    st_global(dB + i, (TOut)(v[t2][i] >> 16));
+                }
+    }
+}
+
+template <typename TOut, int G>
+__device__ __forceinline__ void fused_cta_u8x2(const FusedLaunch& L, const FusedSlot& sp, unsigned cta,
+                                               unsigned char* smem_raw) {
+    static_assert(G == 4, "two groups per warp needs G = 4");
+    constexpr int R = 1 << G;
+    constexpr int NW = fused_warps<G>();
+    constexpr int WS = fused_ws<G>();
+    uint16_t* S = reinterpret_cast<uint16_t*>(smem_raw);  // [u2][t1][WS] (+ K pad)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int N = L.N;
+    const unsigned ntiles = (unsigned)L.ntiles;
+    unsigned unit = cta / ntiles;
+    const int tile = (int)(cta - unit * ntiles);
+    const int wb = L.n - G;  // m0 = 0
+    const int wq1 = (int)(unit & ((1u << wb) - 1));
+    const int wq2 = (int)(unit >> wb);
+    const int d0 = L.gout.base + tile * L.V;
+    const bool swap = sp.swap != 0;
+    const int rs1 = swap ? 1 : N, rs2 = swap ? N : 1;
+
+    if (d0 + L.V <= 2 * N - 2 * (R - 1)) {  // all-zero tile (slopes so far are zero)
+        uint32_t z[R][K];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int i = 0; i < K; ++i) z[r][i] = 0u;
+        store_rows_x2<TOut, G>(L, sp, z, warp, warp + NW, wq1, wq2, rs1, rs2, d0, lane);
+        return;
+    }
+
+    // ---- phase 1: groups u2 = warp (low halves) and warp + 8 (high halves)
+    {
+        const uint8_t* vol = static_cast<const uint8_t*>(sp.in);
+        const int z0 = d0 + lane * K - 2 * N;
+        const long long sx = swap ? sp.map.sy : sp.map.sx;  // stride of the phase-1 axis
+        const long long s2 = swap ? sp.map.sx : sp.map.sy;  // stride of the phase-2 axis
+        const long long rowA = sp.map.o0 + (long long)(warp + (wq2 << G)) * s2 + (long long)(wq1 << G) * sx;
+        const long long offB = (long long)NW * s2;
+        // byte selectors pairing element i of A with element i of B, in load order
+        const uint32_t sel0 = sp.reverse ? 0x6273u : 0x5140u;
+        const uint32_t sel1 = sp.reverse ? 0x4051u : 0x7362u;
+        uint32_t v[R][K];
+        if (sp.mode == kIngestZ) {
+            const bool in = z0 >= 0 && z0 < N;
+            const int zc = in ? z0 : 0;
+#pragma unroll
+            for (int u1 = 0; u1 < R; ++u1) {
+                long long b = rowA + (long long)u1 * sx + (long long)zc * sp.map.sz;
+                if (sp.reverse) b -= K - 1;
+                uint32_t wA = __ldg(reinterpret_cast<const unsigned*>(vol + b));
+                uint32_t wB = __ldg(reinterpret_cast<const unsigned*>(vol + b + offB));
+                wA = in ? wA : 0u;
+                wB = in ? wB : 0u;
+                const uint32_t t0 = __byte_perm(wA, wB, sel0), t1 = __byte_perm(wA, wB, sel1);
+                v[u1][0] = spread_lo(t0);
+                v[u1][1] = spread_hi(t0);
+                v[u1][2] = spread_lo(t1);
+                v[u1][3] = spread_hi(t1);
+            }
+        } else if (sp.mode == kIngestRun) {
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const int z = z0 + i;
+                const bool in = z >= 0 && z < N;
+                long long b = rowA + (long long)(in ? z : 0) * sp.map.sz;
+                if (sp.reverse) b -= R - 1;
+                uint4 qa = __ldg(reinterpret_cast<const uint4*>(vol + b));
+                uint4 qb = __ldg(reinterpret_cast<const uint4*>(vol + b + offB));
+                uint32_t wa[4] = {qa.x, qa.y, qa.z, qa.w}, wbv[4] = {qb.x, qb.y, qb.z, qb.w};
+#pragma unroll
+                for (int wi = 0; wi < 4; ++wi) {
+                    // rows 4 wi .. 4 wi + 3: word wi, or word 3 - wi read backwards
+                    const uint32_t a = in ? (sp.reverse ? wa[3 - wi] : wa[wi]) : 0u;
+                    const uint32_t bb = in ? (sp.reverse ? wbv[3 - wi] : wbv[wi]) : 0u;
+                    const uint32_t t0 = __byte_perm(a, bb, sel0), t1 = __byte_perm(a, bb, sel1);
+                    v[4 * wi][i] = spread_lo(t0);
+                    v[4 * wi + 1][i] = spread_hi(t0);
+                    v[4 * wi + 2][i] = spread_lo(t1);
+                    v[4 * wi + 3][i] = spread_hi(t1);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int u1 = 0; u1 < R; ++u1)
+#pragma unroll
+                for (int i = 0; i < K; ++i) {
+                    const int z = z0 + i;
+                    const bool in = z >= 0 && z < N;
+                    const long long b = rowA + (long long)u1 * sx + (long long)(in ? z : 0) * sp.map.sz;
+                    const uint32_t a = in ? (uint32_t)vol[b] : 0u;
+                    const uint32_t bb = in ? (uint32_t)vol[b + offB] : 0u;
+                    v[u1][i] = a | (bb << 16);
+                }
+        }
+        fwd_all<G, K>(v);
+        if (lane * K < WS) {
+#pragma unroll
+            for (int t1 = 0; t1 < R; ++t1) {
+                const uint2 lo = make_uint2(__byte_perm(v[t1][0], v[t1][1], 0x5410), __byte_perm(v[t1][2], v[t1][3], 0x5410));
+                const uint2 hi = make_uint2(__byte_perm(v[t1][0], v[t1][1], 0x7632), __byte_perm(v[t1][2], v[t1][3], 0x7632));
+                *reinterpret_cast<uint2*>(S + ((warp * R + t1) * WS + lane * K)) = lo;
+                *reinterpret_cast<uint2*>(S + (((warp + NW) * R + t1) * WS + lane * K)) = hi;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 2: t1 = warp (low halves) and warp + 8 (high halves)
+    {
+        uint32_t v[R][K];
+#pragma unroll
+        for (int u2 = 0; u2 < R; ++u2) {
+            // lanes past WS read the next row (or the pad): values they feed are invalid
+            const uint2 a = *reinterpret_cast<const uint2*>(S + ((u2 * R + warp) * WS + lane * K));
+            const uint2 b = *reinterpret_cast<const uint2*>(S + ((u2 * R + warp + NW) * WS + lane * K));
+            v[u2][0] = __byte_perm(a.x, b.x, 0x5410);
+            v[u2][1] = __byte_perm(a.x, b.x, 0x7632);
+            v[u2][2] = __byte_perm(a.y, b.y, 0x5410);
+            v[u2][3] = __byte_perm(a.y, b.y, 0x7632);
+        }
+        fwd_all<G, K>(v);
+        store_rows_x2<TOut, G>(L, sp, v, warp, warp + NW, wq1, wq2, rs1, rs2, d0, lane);
+    }
+}
+
 }  // namespace fused
 }  // namespace drt3d
