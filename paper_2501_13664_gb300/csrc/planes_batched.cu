@@ -100,7 +100,10 @@ __device__ __forceinline__ void run_g(const FusedLaunch& Lg, int slot, unsigned 
     const unsigned nt = (unsigned)L.ntiles;
     for (unsigned t = 0; t < nt; ++t) {
         if (t > 0) __syncthreads();  // the previous tile's phase 2 is done with shared memory
-        fused_cta<TIn, TOut, uint32_t, TS, G, INGEST, true>(L, sp, cta * nt + t, smem);
+        if constexpr (INGEST && G == 4 && std::is_same<TIn, uint8_t>::value && std::is_same<TS, uint16_t>::value)
+            fused_cta_u8x2<TOut, G>(L, sp, cta * nt + t, smem);  // 16-bit sums: two groups per register
+        else
+            fused_cta<TIn, TOut, uint32_t, TS, G, INGEST, true>(L, sp, cta * nt + t, smem);
     }
 }
 
