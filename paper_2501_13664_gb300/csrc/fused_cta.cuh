@@ -245,6 +245,7 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
                                           int slot_z = 0, uint64_t* mbar = nullptr) {
     static_assert(!TMA || (sizeof(TIn) == 2 && !INGEST && sizeof(TS) == 4 && G >= 3),
                   "TMA staging: 16-bit buffer input, 32-bit phase-1 results, G >= 3");
+    // With TMA, `smem_raw` is 128-byte aligned and `mbar` holds 2^G barriers.
     constexpr int R = 1 << G;
     constexpr int NW = fused_warps<G>();
     constexpr int GPW = R / NW > 0 ? R / NW : 1;  // row groups per warp
@@ -307,6 +308,7 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
                 if (lane == 0) tma::mbar_arrive_expect_tx(&mbar[u2], R * kStageElems * 2);
                 __syncwarp();
                 if (lane < R) {
+                    if constexpr (COHERENT) tma::fence_proxy_async_global();  // rows other CTAs wrote
                     const int u1 = lane;
                     const int a2 = sg2 + (u2 << m0) + (wq2 << (m0 + G));
                     const long long row =
@@ -477,6 +479,15 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
         }
     }
     __syncthreads();
+    if constexpr (TMA) {
+        // Every armed barrier has completed (its warp waited above): retire
+        // them before this shared memory is used again.
+        // (After a recorded time-out a load may still be pending: leave them.)
+        if (threadIdx.x == 0 && !(L.status && *(volatile int*)L.status == (int)DRT3D_ERR_TIMEOUT)) {
+#pragma unroll 1
+            for (int g = 0; g < R; ++g) tma::mbar_inval(&mbar[g]);
+        }
+    }
 
     // ---------------- phase 2: transform along axis 2, warp = t1 ----------
 #pragma unroll 1

@@ -31,6 +31,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cuda.h>
+
 #include "drt3d.h"
 
 namespace drt3d {
@@ -203,6 +205,10 @@ cudaError_t launch_planes_fused(const FusedLaunch& L, int G, ElemKind in_kind, E
 bool fused_uses_tma(int G, ElemKind in_kind, bool ingest);
 cudaError_t launch_planes_fused_tma(const FusedLaunch& L, int G, ElemKind out_kind, const void* in_base,
                                     size_t slot_stride, int nslots, cudaStream_t s);
+// The tensor map of those staged loads (x = displacement - base, y = row,
+// z = slot), for launches that keep it in global memory.
+cudaError_t encode_fused_tmap(const FusedLaunch& L, const void* in_base, size_t slot_stride, int nslots,
+                              CUtensorMap* map);
 cudaError_t launch_planes_pass(const PassLaunch& L, int G, drt3d_dtype in_dtype, bool ingest,
                                bool is_float, int nslots, cudaStream_t s);
 cudaError_t launch_planes_adjoint_pass(const PassLaunch& L, int G, bool scatter, bool is_float,

@@ -28,7 +28,9 @@ namespace drt3d {
 constexpr int kBatchMaxPass = 4;
 
 struct BatchVol {
+    CUtensorMap tmap[kBatchMaxPass];  // TMA view of each pass's 16-bit input (passes that stage it)
     FusedLaunch pass[kBatchMaxPass];
+    int tma[kBatchMaxPass];           // pass stages its input through tmap[p]
     int npass;
     int G[kBatchMaxPass];
     int in_kind[kBatchMaxPass], out_kind[kBatchMaxPass];
@@ -81,8 +83,10 @@ __device__ bool wait_counter(const BatchArgs& A, const unsigned* ctr, unsigned t
 // The item's pass header and dodecant slot are copied into registers: read
 // through a global pointer, the compiler would have to reload them after every
 // store (it cannot prove the output buffers do not alias the tables).
-template <typename TIn, typename TOut, typename TS, int G, bool INGEST>
-__device__ __forceinline__ void run_g(const FusedLaunch& Lg, int slot, unsigned cta, unsigned char* smem) {
+template <typename TIn, typename TOut, typename TS, int G, bool INGEST, bool TMA = false>
+__device__ __forceinline__ void run_g(const FusedLaunch& Lg, int slot, unsigned cta, unsigned char* smem,
+                                      const CUtensorMap* tmap = nullptr, uint64_t* mbar = nullptr,
+                                      int* status = nullptr) {
     FusedLaunch L;
     L.N = Lg.N;
     L.n = Lg.n;
@@ -94,13 +98,15 @@ __device__ __forceinline__ void run_g(const FusedLaunch& Lg, int slot, unsigned 
     L.ntiles = Lg.ntiles;
     L.ctas = Lg.ctas;
     L.vec_store = Lg.vec_store;
-    L.status = nullptr;
+    L.status = status;
     const FusedSlot sp = Lg.slot[slot];
     // one item = one unit: all its displacement tiles
     const unsigned nt = (unsigned)L.ntiles;
     for (unsigned t = 0; t < nt; ++t) {
         if (t > 0) __syncthreads();  // the previous tile's phase 2 is done with shared memory
-        if constexpr (INGEST && G == 4 && std::is_same<TIn, uint8_t>::value && std::is_same<TS, uint16_t>::value)
+        if constexpr (TMA)
+            fused_cta<TIn, TOut, uint32_t, TS, G, false, true, true>(L, sp, cta * nt + t, smem, tmap, slot, mbar);
+        else if constexpr (INGEST && G == 4 && std::is_same<TIn, uint8_t>::value && std::is_same<TS, uint16_t>::value)
             fused_cta_u8x2<TOut, G>(L, sp, cta * nt + t, smem);  // 16-bit sums: two groups per register
         else
             fused_cta<TIn, TOut, uint32_t, TS, G, INGEST, true>(L, sp, cta * nt + t, smem);
@@ -117,7 +123,10 @@ __device__ __forceinline__ void run_kind(const FusedLaunch& L, int G, int slot, 
 }
 
 __global__ void __launch_bounds__(256, 2) planes_batched(const __grid_constant__ BatchArgs A) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar[16];
+    // 128-byte aligned for TMA destinations
+    unsigned char* smem = smem_raw + ((128u - (tma::smem_u32(smem_raw) & 127u)) & 127u);
     __shared__ unsigned s_item, s_next;
     __shared__ int s_go, s_seg;
     // The next item is claimed while the current one runs, hiding the
@@ -158,6 +167,20 @@ __global__ void __launch_bounds__(256, 2) planes_batched(const __grid_constant__
         if (p == 0) {
             if (ok == (int)ElemKind::U16) run_kind<uint8_t, uint16_t, uint16_t, true>(L, G, slot, cta, smem);
             else run_kind<uint8_t, uint32_t, uint16_t, true>(L, G, slot, cta, smem);
+        } else if (B.tma[p]) {
+            // 16-bit input staged by TMA (G >= 3)
+            const CUtensorMap* tm = &B.tmap[p];
+            if (G == 4) {
+                if (ok == (int)ElemKind::U16)
+                    run_g<uint16_t, uint16_t, uint32_t, 4, false, true>(L, slot, cta, smem, tm, mbar, A.status);
+                else
+                    run_g<uint16_t, uint32_t, uint32_t, 4, false, true>(L, slot, cta, smem, tm, mbar, A.status);
+            } else {
+                if (ok == (int)ElemKind::U16)
+                    run_g<uint16_t, uint16_t, uint32_t, 3, false, true>(L, slot, cta, smem, tm, mbar, A.status);
+                else
+                    run_g<uint16_t, uint32_t, uint32_t, 3, false, true>(L, slot, cta, smem, tm, mbar, A.status);
+            }
         } else if (ik == (int)ElemKind::U16) {
             if (ok == (int)ElemKind::U16) run_kind<uint16_t, uint16_t, uint32_t, false>(L, G, slot, cta, smem);
             else run_kind<uint16_t, uint32_t, uint32_t, false>(L, G, slot, cta, smem);
@@ -175,7 +198,7 @@ __global__ void __launch_bounds__(256, 2) planes_batched(const __grid_constant__
     }
 }
 
-size_t batched_smem_bytes() { return ((size_t)(1 << 8) * fused_ws<4>() + K) * sizeof(uint32_t); }
+size_t batched_smem_bytes() { return ((size_t)(1 << 8) * fused_ws<4>() + K) * sizeof(uint32_t) + 128; }
 
 }  // namespace
 
@@ -354,6 +377,9 @@ drt3d_status drt3d_batch_bind(drt3d_batch_plan* B, const drt3d_vol_desc* descs, 
                                    : ((p & 1) ? (void*)bufB : (void*)bufA);
             }
             bv.G[p] = ps.G;
+            bv.tma[p] = fused_uses_tma(ps.G, ps.in_kind, ps.ingest) ? 1 : 0;
+            if (bv.tma[p] && encode_fused_tmap(L, L.slot[0].in, 2 * buf, 12, &bv.tmap[p]) != cudaSuccess)
+                return DRT3D_ERR_CUDA;
             bv.in_kind[p] = (int)ps.in_kind;
             bv.out_kind[p] = (int)ps.out_kind;
             bv.ctas[p] = (unsigned)(L.ctas / L.ntiles);

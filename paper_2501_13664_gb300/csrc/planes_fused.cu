@@ -165,8 +165,8 @@ bool fused_uses_tma(int G, ElemKind in_kind, bool ingest) {
     return !ingest && in_kind == ElemKind::U16 && G >= 3;
 }
 
-cudaError_t launch_planes_fused_tma(const FusedLaunch& L, int G, ElemKind out_kind, const void* in_base,
-                                    size_t slot_stride, int nslots, cudaStream_t s) {
+cudaError_t encode_fused_tmap(const FusedLaunch& L, const void* in_base, size_t slot_stride, int nslots,
+                              CUtensorMap* map) {
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return cudaErrorNotSupported;
     // 3-D view of the slots' input rows: x = displacement - base (the stored
@@ -175,11 +175,17 @@ cudaError_t launch_planes_fused_tma(const FusedLaunch& L, int G, ElemKind out_ki
     const cuuint64_t strides[2] = {(cuuint64_t)L.gin.pitch * 2, (cuuint64_t)slot_stride};
     const cuuint32_t box[3] = {(cuuint32_t)kStageElems, 1, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
-    CUtensorMap map;
-    const CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<void*>(in_base), dims, strides, box,
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<void*>(in_base), dims, strides, box,
                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_planes_fused_tma(const FusedLaunch& L, int G, ElemKind out_kind, const void* in_base,
+                                    size_t slot_stride, int nslots, cudaStream_t s) {
+    CUtensorMap map;
+    const cudaError_t e = encode_fused_tmap(L, in_base, slot_stride, nslots, &map);
+    if (e != cudaSuccess) return e;
     const bool to16 = out_kind == ElemKind::U16;
     switch (G) {
     case 3: return to16 ? launch_tma_g<uint16_t, 3>(L, map, nslots, s) : launch_tma_g<uint32_t, 3>(L, map, nslots, s);
