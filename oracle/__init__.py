@@ -89,6 +89,8 @@ def _load():
             "drto_lines_brute_i64": (None, [I, P, P]),
             "drto_lines_cell_i64": (I64, [I, P, I, I, I, I]),
             "drto_lines_alg3_i32": (I, [I, P, P]),
+            "drto_lines_adjoint_brute_i64": (None, [I, P, P]),
+            "drto_lines_adjoint_i32": (I, [I, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -351,6 +353,41 @@ def lines_forward(f: np.ndarray, sectors=range(N_SECTORS), exact: str = "alg3") 
         else:
             outs.append(lines_alg3(g))
     return np.stack(outs)
+
+
+def lines_adjoint_brute_frame(Jbar_k: np.ndarray) -> np.ndarray:
+    """Transposed scatter of eq.(3DfDJT) for one sector frame, int64, (N,N,N)."""
+    N = Jbar_k.shape[0]
+    _check_N(N)
+    jb = np.ascontiguousarray(Jbar_k, dtype=np.int64)
+    g = np.empty((N, N, N), dtype=np.int64)
+    _load().drto_lines_adjoint_brute_i64(N, _ptr(jb), _ptr(g))
+    return g
+
+
+def lines_adjoint_frame(Jbar_k: np.ndarray) -> np.ndarray:
+    """Algorithm 3 reversed with eq.(invmap3DJsummation), one sector frame, int32 wrapping."""
+    N = Jbar_k.shape[0]
+    _check_N(N)
+    jb = np.ascontiguousarray(Jbar_k, dtype=np.int32)
+    g = np.empty((N, N, N), dtype=np.int32)
+    if _load().drto_lines_adjoint_i32(N, _ptr(jb), _ptr(g)) != 0:
+        raise MemoryError("oracle allocation failed")
+    return g
+
+
+def lines_adjoint(Jbar: np.ndarray, sectors=range(N_SECTORS)) -> np.ndarray:
+    """Backprojection of lines summed over sectors (int32 wrapping):
+    f_bar = sum_k (sector k's frame map)^T (J_k^T Jbar[i]), in the given order.
+    ``Jbar`` has shape (len(sectors), N, N, 2N, 2N)."""
+    ks = list(sectors)
+    N = Jbar.shape[1]
+    _check_N(N)
+    acc = np.zeros(N * N * N, dtype=np.int64)
+    for i, k in enumerate(ks):
+        g = lines_adjoint_frame(Jbar[i]).astype(np.int64).ravel()
+        np.add.at(acc, sector_src_index(N, k).ravel(), g)
+    return (acc & 0xFFFFFFFF).astype(np.uint32).view(np.int32).reshape(N, N, N)
 
 
 def lines_cell_global(f: np.ndarray, k: int, s1: int, s2: int, d1: int, d2: int) -> int:

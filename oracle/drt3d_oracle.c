@@ -492,3 +492,81 @@ int drto_lines_alg3_i32(int N, const int32_t* g_, int32_t* J_) {
     free(fm); free(fn);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Lines adjoint (backprojection), definition: the transposed scatter of     */
+/* eq.(3DfDJT) -- every voxel on the line of cell (s1, s2, d1, d2) receives   */
+/* that cell's value:                                                        */
+/*   gbar[x][y][z] = sum_{s1,s2} Jbar[s1][s2][y - l_{s1}(x) + N][z - l_{s2}(x) + N] */
+/* (both displacements are always inside [1, 2N)).  int64.                   */
+/* ------------------------------------------------------------------------ */
+void drto_lines_adjoint_brute_i64(int N, const int64_t* Jbar, int64_t* gbar) {
+    const int n = ilog2(N), D = 2 * N;
+    memset(gbar, 0, sizeof(int64_t) * (size_t)N * N * N);
+    for (int s1 = 0; s1 < N; ++s1)
+        for (int s2 = 0; s2 < N; ++s2)
+            for (int x = 0; x < N; ++x) {
+                const int64_t l1 = drto_lline(n, s1, x), l2 = drto_lline(n, s2, x);
+                for (int y = 0; y < N; ++y)
+                    for (int z = 0; z < N; ++z) {
+                        const int64_t d1 = y - l1 + N, d2 = z - l2 + N;
+                        gbar[((int64_t)x * N + y) * N + z] += Jbar[(((int64_t)s1 * N + s2) * D + d1) * D + d2];
+                    }
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Lines adjoint by the reversed stage loop of Algorithm 3 with              */
+/* eq.(invmap3DJsummation): separateS1S2 transposed (row s1 + (s2 << n) takes */
+/* Jbar[s1][s2]), then for m = n-1 .. 0 each stage-m row pair (v bit 0, v bit */
+/* 1) gathers the four stage-(m+1) rows (l1, l2) it fed: bit 0 unshifted, bit */
+/* 1 at (d1 - sh1, d2 - sh2) with the forward's shifts (reads below 0 are     */
+/* zero); finally the volume is read back from [0:N, N:2N, N:2N].  Same row   */
+/* layout as drto_lines_alg3_i32; int32 wrap.                                */
+/* ------------------------------------------------------------------------ */
+int drto_lines_adjoint_i32(int N, const int32_t* Jbar_, int32_t* gbar_) {
+    const uint32_t* Jbar = (const uint32_t*)Jbar_;
+    uint32_t* gbar = (uint32_t*)gbar_;
+    const int n = ilog2(N), D = 2 * N;
+    const size_t plane = (size_t)D * D, cells = (size_t)N * N * plane;
+    uint32_t* fm = (uint32_t*)calloc(cells, sizeof(uint32_t));
+    uint32_t* fn = (uint32_t*)calloc(cells, sizeof(uint32_t));
+    if (!fm || !fn) { free(fm); free(fn); return -1; }
+    for (int s1 = 0; s1 < N; ++s1)
+        for (int s2 = 0; s2 < N; ++s2)
+            memcpy(fm + (size_t)(s1 + (s2 << n)) * plane, Jbar + ((size_t)s1 * N + s2) * plane,
+                   plane * sizeof(uint32_t));
+    for (int m = n - 1; m >= 0; --m) {
+        const int S = 1 << m, V = 1 << (n - m - 1);
+        memset(fn, 0, cells * sizeof(uint32_t));
+        for (int sg2 = 0; sg2 < S; ++sg2)
+        for (int l2 = 0; l2 < 2; ++l2)
+        for (int sg1 = 0; sg1 < S; ++sg1)
+        for (int l1 = 0; l1 < 2; ++l1)
+        for (int v = 0; v < V; ++v) {
+            const size_t r0 = (size_t)((v << 1) + (sg1 << (n - m)) + (sg2 << n));
+            const size_t r1 = r0 + 1;
+            const size_t ro = (size_t)(v + (l1 << (n - m - 1)) + (sg1 << (n - m)) + (l2 << n) + (sg2 << (n + 1)));
+            const int sh1 = sg1 + l1, sh2 = sg2 + l2;
+            for (int e1 = 0; e1 < D; ++e1) {
+                const uint32_t* po0 = fm + ro * plane + (size_t)e1 * D;
+                const int d1 = e1 - sh1;
+                const uint32_t* po1 = (d1 >= 0) ? fm + ro * plane + (size_t)d1 * D : NULL;
+                uint32_t* q0 = fn + r0 * plane + (size_t)e1 * D;
+                uint32_t* q1 = fn + r1 * plane + (size_t)e1 * D;
+                for (int e2 = 0; e2 < D; ++e2) {
+                    const int d2 = e2 - sh2;
+                    q0[e2] += po0[e2];
+                    if (po1 && d2 >= 0) q1[e2] += po1[d2];
+                }
+            }
+        }
+        uint32_t* t = fm; fm = fn; fn = t;
+    }
+    for (int x = 0; x < N; ++x)
+        for (int y = 0; y < N; ++y)
+            for (int z = 0; z < N; ++z)
+                gbar[((size_t)x * N + y) * N + z] = fm[(size_t)x * plane + (size_t)(N + y) * D + (N + z)];
+    free(fm); free(fn);
+    return 0;
+}

@@ -92,3 +92,50 @@ def test_sector_forward_consistency(oracle_mod):
     np.testing.assert_array_equal(J, Jb)
     for k in (0, 5, 11):
         assert oracle_mod.lines_cell_global(f, k, 3, 6, 9, 4) == int(J[k, 3, 6, 9, 4])
+
+
+# ---------------------------------------------------------------------------
+# Adjoint (eq.(invmap3DJsummation)): pinned to the forward definition by the
+# dot-product identity, then the reversed recursion to the transposed scatter.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N", [2, 4, 8])
+def test_adjoint_brute_is_transpose_of_definition(oracle_mod, N):
+    g = synth.random_int32((N, N, N), 60 + N, -1000, 1000).astype(np.int64)
+    r = synth.random_int32((N, N, 2 * N, 2 * N), 61 + N, -1000, 1000).astype(np.int64)
+    lhs = int((oracle_mod.lines_brute(g) * r).sum())
+    rhs = int((g * oracle_mod.lines_adjoint_brute_frame(r)).sum())
+    assert lhs == rhs
+
+
+@pytest.mark.parametrize("N", [2, 4, 8, 16])
+def test_adjoint_recursion_equals_transposed_scatter(oracle_mod, N):
+    r = synth.random_int32((N, N, 2 * N, 2 * N), 62 + N)
+    want = (oracle_mod.lines_adjoint_brute_frame(r.astype(np.int64)) % (1 << 32)).astype(np.uint32).view(np.int32)
+    np.testing.assert_array_equal(oracle_mod.lines_adjoint_frame(r), want)
+
+
+def test_adjoint_single_cell_backprojects_its_line(oracle_mod):
+    """One unit cell at slopes (s1, s2), displacements (d1, d2) spreads a 1 over
+    exactly the voxels of its digital line y = l_{s1}(x) + d1 - N,
+    z = l_{s2}(x) + d2 - N, computed from eq.(digitalLine) directly."""
+    N, n = 8, 3
+    for s1, s2, d1, d2 in [(0, 0, 9, 12), (5, 2, 8, 10), (7, 7, 3, 1), (3, 6, 12, 15)]:
+        r = np.zeros((N, N, 2 * N, 2 * N), dtype=np.int32)
+        r[s1, s2, d1, d2] = 1
+        g = oracle_mod.lines_adjoint_frame(r)
+        want = np.zeros((N, N, N), dtype=np.int32)
+        for x in range(N):
+            y, z = lline_rec(n, s1, x) + d1 - N, lline_rec(n, s2, x) + d2 - N
+            if 0 <= y < N and 0 <= z < N:
+                want[x, y, z] = 1
+        np.testing.assert_array_equal(g, want)
+
+
+def test_adjoint_sector_sum_matches_global_dot_product(oracle_mod):
+    """<J f, r> = <f, J^T r> over all 12 sectors, through the sector maps."""
+    N = 8
+    f = synth.random_int32((N, N, N), 63, -100, 100)
+    r = synth.random_int32((12, N, N, 2 * N, 2 * N), 64, -100, 100)
+    J = oracle_mod.lines_forward(f).astype(np.int64)
+    fb = oracle_mod.lines_adjoint(r).astype(np.int64)
+    assert int((J * r.astype(np.int64)).sum()) == int((f.astype(np.int64) * fb).sum())
