@@ -474,7 +474,12 @@ def bench_batched(drt3d, synth, dev, tuned) -> dict:
     sizes = synth.c4_sizes()
     vols = [torch.from_numpy(v).to(dev) for v in synth.c4_batch(sizes=sizes)]
     sched = {N: tuple(tuned[N]) for N in set(sizes) if N in tuned}
-    bp = drt3d.BatchPlan(sizes, schedules=sched)
+    bsched = sched
+    if tuned:
+        from paper_2501_13664_gb300 import autotune
+
+        bsched = autotune.tune_batched(sizes)  # splits for the persistent kernel's footprint
+    bp = drt3d.BatchPlan(sizes, schedules=bsched)
     outs = bp.bind(vols)
     plans, wss = {}, {}
     for N in set(sizes):
@@ -507,6 +512,8 @@ def bench_batched(drt3d, synth, dev, tuned) -> dict:
             "batched_volumes_per_s": len(sizes) / (tb / 1000), "one_by_one_volumes_per_s": len(sizes) / (t1 / 1000),
             "speedup": t1 / tb, "floor_gbs_batched": floor / (tb / 1000) / 1e9,
             "launches_batched": 1, "launches_one_by_one": sum(len(plans[N].schedule()) for N in sizes),
+            "schedules_batched": {str(N): list(v) for N, v in sorted(bsched.items())},
+            "schedules_one_by_one": {str(N): list(v) for N, v in sorted(sched.items())},
             "note": "batched = one memset + one persistent kernel, replayed from a CUDA graph; median of 7"}
 
 

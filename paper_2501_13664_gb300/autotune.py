@@ -103,3 +103,55 @@ def tune(Ns, dtype: torch.dtype = torch.uint8, use_cache: bool = True, seed: int
     if use_cache:
         save_cache(cache)
     return best
+
+
+def time_batched(N: int, groups, count: int, dtype: torch.dtype = torch.uint8, reps: int = 5,
+                 seed: int = 11) -> float:
+    """Median milliseconds of one batched launch of ``count`` volumes of size N
+    under ``groups`` (the persistent kernel has one fixed footprint, so the
+    best split can differ from the per-pass launches')."""
+    from . import BatchPlan
+
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    vols = [torch.randint(0, 256, (N, N, N), generator=g, dtype=torch.int32).to(dtype).cuda()
+            for _ in range(count)]
+    bp = BatchPlan([N] * count, dtype=dtype, schedules={N: tuple(groups)})
+    bp.bind(vols)
+    for _ in range(2):
+        bp.run()
+    times = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        bp.run()
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    times.sort()
+    return times[len(times) // 2]
+
+
+def tune_batched(sizes, dtype: torch.dtype = torch.uint8, use_cache: bool = True, max_count: int = 4) -> dict:
+    """{N: best split for the batched launch}, timing up to ``max_count``
+    volumes of each size of ``sizes`` alone."""
+    cache = load_cache() if use_cache else {}
+    best = {}
+    counts = {}
+    for n in sizes:
+        counts[int(n)] = counts.get(int(n), 0) + 1
+    for N in sorted(counts):
+        key = "batched|" + _key(N, dtype)
+        if key in cache:
+            best[N] = tuple(cache[key]["groups"])
+            continue
+        n = N.bit_length() - 1
+        c = min(counts[N], max_count)
+        results = {str(sp): time_batched(N, sp, c, dtype) for sp in splits(n) if len(sp) <= 4}
+        pick = min(results, key=results.get)
+        best[N] = tuple(int(x) for x in pick.strip("()").split(",") if x.strip())
+        cache[key] = {"groups": list(best[N]), "ms": results, "count": c}
+        torch.cuda.empty_cache()
+    if use_cache:
+        save_cache(cache)
+    return best
+

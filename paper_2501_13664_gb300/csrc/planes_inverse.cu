@@ -20,10 +20,14 @@
 // warp.  A lane holds a CH-displacement chunk of both rows of its pair in
 // registers (CH = 8..32, chosen so that one warp's chunks cover a row), forms
 // nD = out_0 - out_1 and the chunk's suffix sums; one warp shuffle scan of the
-// chunk totals turns them into nT = -T.  lo = out_0 - nT
-// goes back over out_0 and nT over out_1; hi[e] = nT[e - S] is then a shifted
-// copy of that row, read as 16-byte vectors at a warp-uniform misalignment
-// and written in place (all reads of a segment before its writes).
+// chunk totals turns them into nT = -T.  lo = out_0 - nT goes back over out_0
+// and nT over out_1.  hi[e] = nT[e - S] is not copied: the slot records the
+// offset S, and whoever reads the row later (the next stage, the range check,
+// the final store) reads element e at e - S.  A stage's pair is either two
+// unshifted rows or two rows at offsets (S, S + 1) (the hi rows of two
+// neighbouring pairs of the previous stage); shifted rows are read as 16-byte
+// vectors from the aligned element below and unpacked at a compile-time
+// misalignment.
 //
 // Shared layout: a row slot holds P prefix chunks (displacements below the
 // stored range, which the shifted copy reads) and NC chunks of CH words.
@@ -68,49 +72,127 @@ __device__ __forceinline__ int word_off(int i, int P) {
 __device__ __forceinline__ uint4 lds4(const uint32_t* s, int off) { return *reinterpret_cast<const uint4*>(s + off); }
 __device__ __forceinline__ void sts4(uint32_t* s, int off, uint4 v) { *reinterpret_cast<uint4*>(s + off) = v; }
 
-// hi[e] = nT[e - S] over a pair's hi row, in place over nT (slot s1), for
-// one compile-time in-vector misalignment RR = (-S) & 3.  Segments go from
-// the top; inside one, every lane reads its whole window before any lane
-// writes.  Lanes past the row read the last chunk's window (broadcast) and
-// store nothing.
-template <int CH, int RR, bool MULTI>
-__device__ __forceinline__ void hi_pass(uint32_t* s1, int S, int P, int NC, int W, int lane) {
-    constexpr int VPC = CH / 4;               // vectors per chunk
-    constexpr int NVEC = RR ? VPC + 1 : VPC;  // vectors covering the window
+// The 4 * NVEC elements of a row from the 4-aligned physical element
+// `start` (>= -CH P), NVEC = CH/4 or CH/4 + 1: crosses at most one chunk
+// boundary.
+template <int CH, int NVEC>
+__device__ __forceinline__ void read_window(const uint32_t* s, int start, int P, uint32_t (&src)[4 * NVEC]) {
+    constexpr int VPC = CH / 4;
+    const int w0 = word_off<CH>(start, P);
+    const int kb = VPC - (((start + P * CH) % CH) >> 2);  // vectors before the next chunk starts
+#pragma unroll
+    for (int t = 0; t < NVEC; ++t) {
+        const uint4 w = lds4(s, w0 + 4 * t + (t >= kb ? 4 : 0));
+        src[4 * t] = w.x; src[4 * t + 1] = w.y; src[4 * t + 2] = w.z; src[4 * t + 3] = w.w;
+    }
+}
+
+// Logical chunk c of both rows of a pair: a = out_0, x = out_0 - out_1.
+// SH: the rows sit at offsets (off0, off0 + 1) with RR0 = (-off0) & 3;
+// otherwise both are unshifted.
+template <int CH, bool SH, int RR0>
+__device__ __forceinline__ void load_pair(const uint32_t* s0, const uint32_t* s1, int c, int off0, int P,
+                                          uint32_t (&a)[CH], uint32_t (&x)[CH]) {
+    constexpr int VPC = CH / 4;
+    if constexpr (!SH) {
+        const int cw = (c + P) * (CH + 4);
+#pragma unroll
+        for (int kv = 0; kv < VPC; ++kv) {
+            const uint4 A = lds4(s0, cw + 4 * kv);
+            const uint4 B = lds4(s1, cw + 4 * kv);
+            a[4 * kv] = A.x; a[4 * kv + 1] = A.y; a[4 * kv + 2] = A.z; a[4 * kv + 3] = A.w;
+            x[4 * kv] = A.x - B.x; x[4 * kv + 1] = A.y - B.y; x[4 * kv + 2] = A.z - B.z; x[4 * kv + 3] = A.w - B.w;
+        }
+    } else {
+        constexpr int RR1 = (RR0 + 3) & 3;  // (-(off0 + 1)) & 3
+        constexpr int N0 = RR0 ? VPC + 1 : VPC, N1 = RR1 ? VPC + 1 : VPC;
+        uint32_t w0[4 * N0], w1[4 * N1];
+        read_window<CH, N0>(s0, CH * c - off0 - RR0, P, w0);
+        read_window<CH, N1>(s1, CH * c - off0 - 1 - RR1, P, w1);
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+            a[k] = w0[k + RR0];
+            x[k] = w0[k + RR0] - w1[k + RR1];
+        }
+    }
+}
+
+// One pair of one stage: lo over out_0's slot, nT over out_1's slot (with
+// its prefix below the stored range).  Segments of 32 chunks from the top;
+// inside one, every lane reads before any lane writes (shifted reads reach
+// lower chunks, writes go to the lane's own chunk).
+template <int CH, bool MULTI, bool SH, int RR0>
+__device__ __forceinline__ void stage_pair(uint32_t* s0, uint32_t* s1, int off0, int P, int NC, int base, int lane) {
+    constexpr int VPC = CH / 4;
+    constexpr int RUN = CH / 4;  // suffix-sum run length (4 runs per chunk)
     const int nseg = MULTI ? (NC + 31) / 32 : 1;
+    uint32_t seg_carry = 0, first = 0;
 #pragma unroll 1
     for (int sgm = nseg - 1; sgm >= 0; --sgm) {
         const int c = sgm * 32 + lane;
-        const int ce = c < NC ? c : NC - 1;
-        const int pa = CH * ce - S - RR;  // aligned window start (element)
-        const int w0 = word_off<CH>(pa, P);
-        const int kb = VPC - (((pa + P * CH) % CH) >> 2);  // vectors before the next chunk starts
-        uint32_t src[4 * NVEC];
+        const bool live = c < NC;
+        uint32_t a[CH], x[CH];
+        load_pair<CH, SH, RR0>(s0, s1, live ? c : NC - 1, off0, P, a, x);
+        // Chunk suffix sums as 4 independent runs (short dependency chains),
+        // then the runs' carries.
 #pragma unroll
-        for (int t = 0; t < NVEC; ++t) {
-            const uint4 w = lds4(s1, w0 + 4 * t + (t >= kb ? 4 : 0));
-            src[4 * t] = w.x; src[4 * t + 1] = w.y; src[4 * t + 2] = w.z; src[4 * t + 3] = w.w;
+        for (int k = RUN - 2; k >= 0; --k)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) x[RUN * b + k] += x[RUN * b + k + 1];
+        uint32_t rc[4];
+        rc[3] = 0u;
+        rc[2] = x[3 * RUN];
+        rc[1] = rc[2] + x[2 * RUN];
+        rc[0] = rc[1] + x[RUN];
+        const uint32_t tot = live ? x[0] + rc[0] : 0u;
+        uint32_t y = tot;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t z = __shfl_down_sync(0xffffffffu, y, off);
+            if (lane + off < 32) y += z;
         }
-        __syncwarp();
-        uint32_t* dst = s1 + (c + P) * (CH + 4);
-        const int past = W - CH * c;  // elements of this chunk inside the stored width
-        if (past >= CH) {
+        const uint32_t carry = y - tot + seg_carry;
 #pragma unroll
-            for (int kv = 0; kv < VPC; ++kv)
-                sts4(dst, 4 * kv,
-                     make_uint4(src[4 * kv + RR], src[4 * kv + 1 + RR], src[4 * kv + 2 + RR], src[4 * kv + 3 + RR]));
-        } else if (past > 0) {
+        for (int b = 0; b < 4; ++b) rc[b] += carry;
 #pragma unroll
-            for (int k = 0; k < CH; ++k) dst[k] = k < past ? src[k + RR] : 0u;
+        for (int k = 0; k < CH; ++k) {
+            x[k] += rc[k / RUN];  // nT
+            a[k] -= x[k];         // lo = out_0 + T
         }
-        __syncwarp();
+        first = x[0];
+        if constexpr (SH) __syncwarp();  // all shifted reads of the segment before its writes
+        if (live) {
+            const int cw = (c + P) * (CH + 4);
+#pragma unroll
+            for (int kv = 0; kv < VPC; ++kv) {
+                sts4(s0, cw + 4 * kv, make_uint4(a[4 * kv], a[4 * kv + 1], a[4 * kv + 2], a[4 * kv + 3]));
+                sts4(s1, cw + 4 * kv, make_uint4(x[4 * kv], x[4 * kv + 1], x[4 * kv + 2], x[4 * kv + 3]));
+            }
+        }
+        seg_carry += __shfl_sync(0xffffffffu, y, 0);
+        if constexpr (SH && MULTI) __syncwarp();
+    }
+    // Prefix below the stored range: T is constant (= T[0]) there, where
+    // Delta vanishes, and hi is 0 below displacement 0.
+    const uint32_t nT0 = __shfl_sync(0xffffffffu, first, 0);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const int v = lane + 32 * it;
+        const int i = -CH * P + 4 * v;
+        const uint32_t f = base + i >= 0 ? nT0 : 0u;
+        if (v < VPC * P) sts4(s1, word_off<CH>(i, P), make_uint4(f, f, f, f));
+    }
+    for (int v = lane + 64; v < VPC * P; v += 32) {
+        const int i = -CH * P + 4 * v;
+        const uint32_t f = base + i >= 0 ? nT0 : 0u;
+        sts4(s1, word_off<CH>(i, P), make_uint4(f, f, f, f));
     }
 }
 
 // MULTI: rows of more than 32 chunks, scanned in segments of 32 chunks from
 // the top with a carry; otherwise one segment.
 template <int G, int CH, bool MULTI>
-__global__ void __launch_bounds__(inv_warps(G) * 32, (G >= 4 ? 2 : 4))
+__global__ void __launch_bounds__(inv_warps(G) * 32, (G >= 4 ? (CH <= 16 ? 3 : 2) : 4))
 planes_inv_pass(const __grid_constant__ InvLaunch L) {
     constexpr int R = 1 << G;
     constexpr int NW = inv_warps(G);
@@ -120,6 +202,7 @@ planes_inv_pass(const __grid_constant__ InvLaunch L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint32_t* rows = reinterpret_cast<uint32_t*>(smem_raw);
     __shared__ int slot[R];
+    __shared__ int slot_off[R];  // offset of the row a slot holds (element e at e - offset)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = L.N, m0 = L.m0;
@@ -168,10 +251,12 @@ planes_inv_pass(const __grid_constant__ InvLaunch L) {
             }
         }
     }
-    if (threadIdx.x < R) slot[threadIdx.x] = threadIdx.x;
+    if (threadIdx.x < R) {
+        slot[threadIdx.x] = threadIdx.x;
+        slot_off[threadIdx.x] = 0;
+    }
     __syncthreads();
 
-    const int nseg = MULTI ? (NC + 31) / 32 : 1;
 #pragma unroll 1
     for (int J = G - 1; J >= 0; --J) {
         const int half = 1 << J;
@@ -180,8 +265,11 @@ planes_inv_pass(const __grid_constant__ InvLaunch L) {
             const int q = p >> J, tau = p & (half - 1);
             const int r0 = 2 * tau + (q << (J + 1));  // rows of stage J+1 (within the unit)
             const int S = (sg << J) + tau;            // slope so far at global stage m0 + J
-            uint32_t* s0 = rows + slot[r0] * RS;
-            uint32_t* s1 = rows + slot[r0 + 1] * RS;
+            const int sl0 = slot[r0], sl1 = slot[r0 + 1];
+            uint32_t* s0 = rows + sl0 * RS;
+            uint32_t* s1 = rows + sl1 * RS;
+            const int off1 = slot_off[sl1];
+            const int off0 = off1 ? off1 - 1 : 0;  // the pair is (0, 0) or (off, off + 1)
 
             // Data in the range has Delta = 0 past 3N - 1 - S; check it there.
             {
@@ -190,88 +278,26 @@ planes_inv_pass(const __grid_constant__ InvLaunch L) {
 #pragma unroll
                 for (int it = 0; it < 4; ++it) {  // S < 128: at most 4 rounds
                     const int i = from + lane + 32 * it;
-                    if (i < W) bad |= s0[word_off<CH>(i, P)] != s1[word_off<CH>(i, P)];
+                    if (i < W) bad |= s0[word_off<CH>(i - off0, P)] != s1[word_off<CH>(i - off1, P)];
                 }
                 for (int i = from + 128 + lane; i < W; i += 32)
-                    bad |= s0[word_off<CH>(i, P)] != s1[word_off<CH>(i, P)];
+                    bad |= s0[word_off<CH>(i - off0, P)] != s1[word_off<CH>(i - off1, P)];
                 if (__any_sync(0xffffffffu, bad) && lane == 0) flag(L.status, DRT3D_ERR_NOT_IN_RANGE);
             }
-
-            // nT = -(suffix sums of Delta); lo = out_0 - nT.  Segments of 32
-            // chunks from the top; lane L owns chunk 32 * seg + L.
-            uint32_t seg_carry = 0, first = 0;
-#pragma unroll 1
-            for (int sgm = nseg - 1; sgm >= 0; --sgm) {
-                const int c = sgm * 32 + lane;
-                const bool live = c < NC;
-                const int cw = ((live ? c : NC - 1) + P) * (CH + 4);  // chunk start (words)
-                uint32_t a[CH], x[CH];
-#pragma unroll
-                for (int kv = 0; kv < VPC; ++kv) {
-                    const uint4 A = lds4(s0, cw + 4 * kv);
-                    const uint4 Bv = lds4(s1, cw + 4 * kv);
-                    a[4 * kv] = A.x; a[4 * kv + 1] = A.y; a[4 * kv + 2] = A.z; a[4 * kv + 3] = A.w;
-                    x[4 * kv] = A.x - Bv.x; x[4 * kv + 1] = A.y - Bv.y;
-                    x[4 * kv + 2] = A.z - Bv.z; x[4 * kv + 3] = A.w - Bv.w;
-                }
-                // Chunk suffix sums as 4 independent runs (short dependency
-                // chains), then the runs' carries.
-#pragma unroll
-                for (int k = RUN - 2; k >= 0; --k)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) x[RUN * b + k] += x[RUN * b + k + 1];
-                uint32_t rc[4];
-                rc[3] = 0u;
-                rc[2] = x[3 * RUN];
-                rc[1] = rc[2] + x[2 * RUN];
-                rc[0] = rc[1] + x[RUN];
-                const uint32_t tot = live ? x[0] + rc[0] : 0u;
-                uint32_t y = tot;
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const uint32_t z = __shfl_down_sync(0xffffffffu, y, off);
-                    if (lane + off < 32) y += z;
-                }
-                const uint32_t carry = y - tot + seg_carry;
-#pragma unroll
-                for (int b = 0; b < 4; ++b) rc[b] += carry;
-#pragma unroll
-                for (int k = 0; k < CH; ++k) {
-                    x[k] += rc[k / RUN];  // nT
-                    a[k] -= x[k];         // lo = out_0 + T
-                }
-                first = x[0];
-                if (live) {
-#pragma unroll
-                    for (int kv = 0; kv < VPC; ++kv) {
-                        sts4(s0, cw + 4 * kv, make_uint4(a[4 * kv], a[4 * kv + 1], a[4 * kv + 2], a[4 * kv + 3]));
-                        sts4(s1, cw + 4 * kv, make_uint4(x[4 * kv], x[4 * kv + 1], x[4 * kv + 2], x[4 * kv + 3]));
-                    }
-                }
-                seg_carry += __shfl_sync(0xffffffffu, y, 0);
-            }
-            // Prefix below the stored range: T is constant (= T[0]) there,
-            // where Delta vanishes, and hi is 0 below displacement 0.
-            const uint32_t nT0 = __shfl_sync(0xffffffffu, first, 0);
-#pragma unroll
-            for (int it = 0; it < 2; ++it) {
-                const int v = lane + 32 * it;
-                const int i = -CH * P + 4 * v;
-                const uint32_t f = base + i >= 0 ? nT0 : 0u;
-                if (v < VPC * P) sts4(s1, word_off<CH>(i, P), make_uint4(f, f, f, f));
-            }
-            for (int v = lane + 64; v < VPC * P; v += 32) {
-                const int i = -CH * P + 4 * v;
-                const uint32_t f = base + i >= 0 ? nT0 : 0u;
-                sts4(s1, word_off<CH>(i, P), make_uint4(f, f, f, f));
-            }
             __syncwarp();
-            // hi[e] = nT[e - S], in place over nT.
-            switch ((-S) & 3) {
-            case 0: hi_pass<CH, 0, MULTI>(s1, S, P, NC, W, lane); break;
-            case 1: hi_pass<CH, 1, MULTI>(s1, S, P, NC, W, lane); break;
-            case 2: hi_pass<CH, 2, MULTI>(s1, S, P, NC, W, lane); break;
-            default: hi_pass<CH, 3, MULTI>(s1, S, P, NC, W, lane); break;
+            if (off1 == 0) {
+                stage_pair<CH, MULTI, false, 0>(s0, s1, 0, P, NC, base, lane);
+            } else {
+                switch ((-off0) & 3) {
+                case 0: stage_pair<CH, MULTI, true, 0>(s0, s1, off0, P, NC, base, lane); break;
+                case 1: stage_pair<CH, MULTI, true, 1>(s0, s1, off0, P, NC, base, lane); break;
+                case 2: stage_pair<CH, MULTI, true, 2>(s0, s1, off0, P, NC, base, lane); break;
+                default: stage_pair<CH, MULTI, true, 3>(s0, s1, off0, P, NC, base, lane); break;
+                }
+            }
+            if (lane == 0) {
+                slot_off[sl0] = 0;  // lo, in place
+                slot_off[sl1] = S;  // hi[e] = nT[e - S]
             }
         }
         __syncthreads();
@@ -293,6 +319,7 @@ planes_inv_pass(const __grid_constant__ InvLaunch L) {
 
     // ---- store the unit's input rows a(u) = sg + (u << m0) + (w << (m0 + G)).
     // Recovered values below the output geometry's lower bound must vanish.
+    // A row at offset `off` holds element i at i - off.
     bool bad = false;
     if (!L.scatter) {
         const int lo_out = L.lo_out;
@@ -303,11 +330,18 @@ planes_inv_pass(const __grid_constant__ InvLaunch L) {
             const long long row = (long long)a * rs_axis + (long long)j * rs_other;
             uint32_t* dst = out + row * L.gout.pitch - L.gout.base + base;  // element i of the stored row
             const uint32_t* srow = rows + slot[u] * RS;
+            const int off = slot_off[slot[u]];
             for (int v = lane; 4 * v < W; v += 32) {
                 const int i = 4 * v;
                 const int d = base + i;
-                const uint4 w = lds4(srow, word_off<CH>(i, P));
-                const uint32_t e[4] = {w.x, w.y, w.z, w.w};
+                uint32_t e[4];
+                if ((off & 3) == 0) {
+                    const uint4 w = lds4(srow, word_off<CH>(i - off, P));
+                    e[0] = w.x; e[1] = w.y; e[2] = w.z; e[3] = w.w;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) e[k] = srow[word_off<CH>(i + k - off, P)];
+                }
                 if (d < lo_out) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
@@ -315,7 +349,7 @@ planes_inv_pass(const __grid_constant__ InvLaunch L) {
                 }
                 if (d >= L.gout.base) {
                     if (vec_out && i + 4 <= W) {
-                        *reinterpret_cast<uint4*>(dst + i) = w;
+                        *reinterpret_cast<uint4*>(dst + i) = make_uint4(e[0], e[1], e[2], e[3]);
                     } else {
 #pragma unroll
                         for (int k = 0; k < 4; ++k)
@@ -336,13 +370,20 @@ planes_inv_pass(const __grid_constant__ InvLaunch L) {
                 const int xp = L.axis == 0 ? a : j, yp = L.axis == 0 ? j : a;
                 const long long rb = M.o0 + xp * M.sx + yp * M.sy;
                 const uint32_t* srow = rows + slot[u] * RS;
+                const int off = slot_off[slot[u]];
                 for (int v = lane; 4 * v < W; v += 32) {
                     const int i = 4 * v;
                     const int d = base + i;
-                    const uint4 w = lds4(srow, word_off<CH>(i, P));
-                    const uint32_t e[4] = {w.x, w.y, w.z, w.w};
+                    uint32_t e[4];
+                    if ((off & 3) == 0) {
+                        const uint4 w = lds4(srow, word_off<CH>(i - off, P));
+                        e[0] = w.x; e[1] = w.y; e[2] = w.z; e[3] = w.w;
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) e[k] = srow[word_off<CH>(i + k - off, P)];
+                    }
                     if (M.sz == 1 && d >= 2 * N && i + 4 <= W && ((rb + d - 2 * N) & 3) == 0) {
-                        *reinterpret_cast<uint4*>(vol + rb + (d - 2 * N)) = w;
+                        *reinterpret_cast<uint4*>(vol + rb + (d - 2 * N)) = make_uint4(e[0], e[1], e[2], e[3]);
                     } else {
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
@@ -358,7 +399,7 @@ planes_inv_pass(const __grid_constant__ InvLaunch L) {
             for (int idx = threadIdx.x; idx < R * W; idx += NT) {
                 const int i = idx / R, u = idx - i * R;
                 const int d = base + i;
-                const uint32_t e = rows[slot[u] * RS + word_off<CH>(i, P)];
+                const uint32_t e = rows[slot[u] * RS + word_off<CH>(i - slot_off[slot[u]], P)];
                 if (d < 2 * N) {
                     bad |= e != 0u;
                 } else {
