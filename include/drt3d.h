@@ -84,7 +84,8 @@ typedef enum drt3d_op {
     DRT3D_OP_PLANES_FORWARD = 0,
     DRT3D_OP_PLANES_ADJOINT = 1,
     DRT3D_OP_PLANES_INVERSE = 2,
-    DRT3D_OP_LINES_FORWARD = 3
+    DRT3D_OP_LINES_FORWARD = 3,
+    DRT3D_OP_LINES_ADJOINT = 4
 } drt3d_op;
 
 #define DRT3D_ALL_DODECANTS 0xFFFu
@@ -164,6 +165,20 @@ drt3d_status drt3d_planes_inverse(const drt3d_plan* plan, const int32_t* d_R, in
 drt3d_status djt3d_lines_forward(const drt3d_plan* plan, const void* d_in, int32_t* d_out,
                                  uint32_t sector_mask, void* d_ws, size_t ws_bytes,
                                  cudaStream_t stream);
+
+/* Adjoint (backprojection) of djt3d_lines_forward (eq.(invmap3DJsummation):
+ * Algorithm 3's stage loop reversed; reads below displacement 0 are zero):
+ *   d_vol = sum over selected k, in increasing k, of (sector k's frame map)^T
+ *           (J_k^T d_cot[k]).
+ *   d_cot : popcount(sector_mask) blocks of N*N*2N*2N int32, J[k][s1][s2][d1][d2].
+ *   d_vol : N^3 int32 volume f[x][y][z] (original frame), overwritten.
+ *   d_ws, ws_bytes: workspace, >= drt3d_workspace_bytes(LINES_ADJOINT)
+ *            (two stage buffers per sector: 1.6 GB per sector at N = 128).
+ * Plan dtype must be I32; N <= 256.  Exact in wrapping int32 and deterministic
+ * (every output is a gather; no atomics).  Errors: INVALID_ARG, DTYPE, SIZE,
+ * ALIGN, WORKSPACE, CUDA. */
+drt3d_status djt3d_lines_adjoint(const drt3d_plan* plan, const int32_t* d_cot, int32_t* d_vol,
+                                 uint32_t sector_mask, void* d_ws, size_t ws_bytes, cudaStream_t stream);
 
 /* Stage-fusion schedule of the planes forward: the n = log2 N stages of
  * eq.(map3D) run in `ngroups` passes of G[0], G[1], ... stages on both axes

@@ -298,6 +298,28 @@ def lines_forward(vol: torch.Tensor, sectors=ALL, out: torch.Tensor | None = Non
     return out.to("cpu") if host else out
 
 
+def lines_adjoint(cot: torch.Tensor, sectors=ALL, out: torch.Tensor | None = None,
+                  workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """Backprojection of lines (eq.(invmap3DJsummation)) summed over the sectors,
+    int32: ``cot`` is (len(sectors), N, N, 2N, 2N)."""
+    cot_d, host = _to_device(cot)
+    if cot_d.dtype != torch.int32:
+        raise TypeError("the lines adjoint takes int32 cotangents")
+    m = _mask(sectors)
+    N = int(cot_d.shape[1])
+    if cot_d.dim() != 5 or cot_d.shape[0] != _count(m) or tuple(cot_d.shape[2:]) != (N, 2 * N, 2 * N):
+        raise ValueError(f"cotangent shape {tuple(cot_d.shape)} does not match {_count(m)} sectors")
+    cot_d = cot_d.contiguous()
+    plan = get_plan(N, torch.int32)
+    if out is None:
+        out = torch.empty((N, N, N), dtype=torch.int32, device=cot_d.device)
+    ws = workspace if workspace is not None else plan.workspace("lines_adjoint")
+    _abi.check(plan._lib.djt3d_lines_adjoint(plan.handle, cot_d.data_ptr(), out.data_ptr(), m,
+                                             ws.data_ptr(), ws.numel(), _stream()),
+               "djt3d_lines_adjoint")
+    return out.to("cpu") if host else out
+
+
 class PlanesTransform(torch.autograd.Function):
     """Differentiable 3D DRT of planes for float32 volumes.
 

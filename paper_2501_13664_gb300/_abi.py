@@ -31,6 +31,7 @@ SIGNATURES = {
     "drt3d_planes_adjoint": (I, [P, P, P, U32, P, SZ, P]),
     "drt3d_planes_inverse": (I, [P, P, I, P, P, SZ, P]),
     "djt3d_lines_forward": (I, [P, P, P, U32, P, SZ, P]),
+    "djt3d_lines_adjoint": (I, [P, P, P, U32, P, SZ, P]),
     "drt3d_get_device_error": (I, [P, P]),
     "drt3d_status_string": (ctypes.c_char_p, [I]),
     "drt3d_set_profiling": (I, [P, I]),
@@ -59,7 +60,7 @@ STATUS = {
     11: "DRT3D_ERR_SCRATCH_LIMIT",
 }
 DTYPES = {"u8": 0, "i16": 1, "i32": 2, "f32": 3}
-OPS = {"planes_forward": 0, "planes_adjoint": 1, "planes_inverse": 2, "lines_forward": 3}
+OPS = {"planes_forward": 0, "planes_adjoint": 1, "planes_inverse": 2, "lines_forward": 3, "lines_adjoint": 4}
 
 
 class DRT3DError(RuntimeError):

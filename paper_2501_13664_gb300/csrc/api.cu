@@ -227,6 +227,18 @@ static size_t djt_buf_bytes(int N) {
     return align_up((size_t)(1LL << (n + m)) * pitch * pitch * 4, 256);
 }
 
+// Lines adjoint: stage m's window [base_m, 2N)^2 (full at m = n), rows
+// 2^(n + m); per slot two buffers for the alternating stages n-1, n-2, ...
+static int djt_adj_base(int N, int m) { return m >= ilog2(N) ? 0 : djt_base(N, m); }
+static size_t djt_adj_stage_bytes(int N, int m) {
+    const long long pitch = 2LL * N - djt_adj_base(N, m);
+    return align_up((size_t)(1LL << (ilog2(N) + m)) * pitch * pitch * 4, 256);
+}
+static size_t djt_adj_slot_bytes(int N) {
+    const int n = ilog2(N);
+    return djt_adj_stage_bytes(N, n - 1) + (n >= 2 ? djt_adj_stage_bytes(N, n - 2) : 0);
+}
+
 static size_t planes_buf_bytes(const drt3d_plan* P) {
     return align_up(P->planes.buf_elems * 4, 256);
 }
@@ -371,6 +383,9 @@ drt3d_status drt3d_workspace_bytes(const drt3d_plan* P, int op, size_t* bytes) {
         return DRT3D_OK;
     case DRT3D_OP_LINES_FORWARD:
         *bytes = (size_t)kMaxSlots * djt_buf_bytes(P->N);
+        return DRT3D_OK;
+    case DRT3D_OP_LINES_ADJOINT:
+        *bytes = (size_t)kMaxSlots * djt_adj_slot_bytes(P->N);
         return DRT3D_OK;
     }
     return DRT3D_ERR_INVALID_ARG;
@@ -603,6 +618,71 @@ drt3d_status djt3d_lines_forward(const drt3d_plan* P, const void* d_in, int32_t*
         prof_end(P, stream);
         m0 = m1;
     }
+    return DRT3D_OK;
+}
+
+drt3d_status djt3d_lines_adjoint(const drt3d_plan* P, const int32_t* d_cot, int32_t* d_vol, uint32_t mask,
+                                 void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!P || !d_cot || !d_vol) return DRT3D_ERR_INVALID_ARG;
+    if (mask == 0 || (mask & ~DRT3D_ALL_SECTORS)) return DRT3D_ERR_INVALID_ARG;
+    if (P->dtype != DRT3D_I32) return DRT3D_ERR_DTYPE;
+    if (P->N > 256) return DRT3D_ERR_SIZE;
+    if (!aligned16(d_cot) || !aligned16(d_vol) || !aligned16(d_ws)) return DRT3D_ERR_ALIGN;
+    const int N = P->N, n = P->n;
+    const int nslots = popcount12(mask);
+    const size_t slot_bytes = djt_adj_slot_bytes(N);
+    if (!d_ws || ws_bytes < (size_t)nslots * slot_bytes) return DRT3D_ERR_WORKSPACE;
+    const long long cot_block = 4LL * N * N * N * N;  // elements per sector
+    char* ws = static_cast<char*>(d_ws);
+    // stage m lives in buffer (n - 1 - m) & 1 of its slot
+    auto stage_buf = [&](int slot, int m) -> uint32_t* {
+        char* b = ws + (size_t)slot * slot_bytes + (((n - 1 - m) & 1) ? djt_adj_stage_bytes(N, n - 1) : 0);
+        return reinterpret_cast<uint32_t*>(b);
+    };
+    DjtAdjGather Gt{};
+    int i = 0;
+    for (int k = 0; k < 12; ++k) {
+        if (!((mask >> k) & 1)) continue;
+        Gt.sector[i] = k;
+        ++i;
+    }
+    for (int m = n - 1; m >= 0; --m) {
+        DjtAdjLaunch L{};
+        for (int s = 0; s < nslots; ++s) {
+            L.in[s] = (m == n - 1) ? reinterpret_cast<const uint32_t*>(d_cot + (size_t)s * cot_block)
+                                   : stage_buf(s, m + 1);
+            L.out[s] = stage_buf(s, m);
+        }
+        L.N = N;
+        L.n = n;
+        L.m = m;
+        L.in_base = djt_adj_base(N, m + 1);
+        L.in_pitch = 2 * N - L.in_base;
+        L.in_plane = (long long)L.in_pitch * L.in_pitch;
+        L.out_base = djt_adj_base(N, m);
+        L.out_pitch = 2 * N - L.out_base;
+        L.out_plane = (long long)L.out_pitch * L.out_pitch;
+        L.D1 = 2 * N - L.out_base;
+        const int lanes_w = 32 * djt_adj_lanes_k();
+        L.ntiles = (L.out_pitch + lanes_w - 1) / lanes_w;
+        L.items = (1LL << (2 * m)) * (1LL << (n - m - 1)) * L.D1 * L.ntiles;
+        char nm[40];
+        std::snprintf(nm, sizeof nm, "djt_adj_stage m=%d", m);
+        const double in_b = (double)(1LL << (n + m + 1)) * L.in_plane * 4;
+        const double out_b = (double)(1LL << (n + m)) * L.out_plane * 4;
+        prof_begin(P, stream, nm, nslots * (in_b + out_b));
+        if (launch_djt_adj_stage(L, nslots, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+        prof_end(P, stream);
+    }
+    for (int s = 0; s < nslots; ++s) Gt.frame[s] = stage_buf(s, 0);
+    Gt.nslots = nslots;
+    Gt.N = N;
+    Gt.base = djt_adj_base(N, 0);
+    Gt.pitch = 2 * N - Gt.base;
+    Gt.out = d_vol;
+    prof_begin(P, stream, "djt_adj_gather", (double)nslots * N * N * N * 4 + (double)N * N * N * 4);
+    if (launch_djt_adj_gather(Gt, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+    prof_end(P, stream);
     return DRT3D_OK;
 }
 

@@ -193,6 +193,31 @@ struct DjtLaunch {
     long long warps;         // warps per slot
 };
 int djt_lanes_k(int G, int width);
+
+// One stage of the lines adjoint, stage m + 1 -> m (djt_adjoint.cu).
+struct DjtAdjLaunch {
+    const uint32_t* in[kMaxSlots];  // stage m + 1 rows per slot
+    uint32_t* out[kMaxSlots];       // stage m rows per slot
+    int N, n, m;
+    int in_base, in_pitch;          // stage m + 1 window [in_base, 2N)^2
+    long long in_plane;
+    int out_base, out_pitch;        // stage m window
+    long long out_plane;
+    int D1, ntiles;                 // e1 rows and e2 tiles of a stage-m plane
+    long long items;                // warps per slot
+};
+// Sum of the selected sectors' frame volumes (stage-0 windows) in the
+// original frame.
+struct DjtAdjGather {
+    const uint32_t* frame[kMaxSlots];
+    int sector[kMaxSlots];
+    int nslots, N;
+    int base, pitch;                // stage-0 window
+    int32_t* out;
+};
+cudaError_t launch_djt_adj_stage(const DjtAdjLaunch& L, int nslots, cudaStream_t s);
+cudaError_t launch_djt_adj_gather(const DjtAdjGather& L, cudaStream_t s);
+int djt_adj_lanes_k();
 cudaError_t launch_djt_pass(const DjtLaunch& L, int G, int K, drt3d_dtype in_dtype, bool ingest, bool final_,
                             int nslots, cudaStream_t s);
 
