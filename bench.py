@@ -530,9 +530,20 @@ def bench_lines(drt3d, synth, dev) -> dict:
     run()
     t = sorted(_event_ms(run, 5))[2]
     floor = 12.0 * N * N * (2 * N) * (2 * N) * 4 + N ** 3 * 2
-    del out
+    del ws
+    # adjoint (backprojection) of the same 12 sectors, the transform as cotangent
+    aplan = drt3d.get_plan(N, torch.int32)
+    aws = aplan.workspace("lines_adjoint")
+    vb = torch.empty((N, N, N), dtype=torch.int32, device=dev)
+    arun = lambda: drt3d.lines_adjoint(out, drt3d.ALL, out=vb, workspace=aws)  # noqa: E731
+    arun()
+    ta = sorted(_event_ms(arun, 5))[2]
+    afloor = 12.0 * N * N * (2 * N) * (2 * N) * 4 + N ** 3 * 4
+    del out, aws
     return {"ms": t, "sectors_per_s": 12 / (t / 1000), "floor_gbs": floor / (t / 1000) / 1e9,
-            "workload": "N=128 int16 uniform 0..1023 + 32 lines, 12 sectors, int32 out"}
+            "adjoint_ms": ta, "adjoint_floor_gbs": afloor / (ta / 1000) / 1e9,
+            "workload": "N=128 int16 uniform 0..1023 + 32 lines, 12 sectors, int32 out; adjoint of that "
+                        "transform back to an int32 volume"}
 
 
 def bench_lsq(drt3d, synth, dev) -> dict:

@@ -413,6 +413,58 @@ def planes_cell_global(f: np.ndarray, k: int, s1: int, s2: int, d: int) -> int:
 
 
 # --------------------------------------------------------------------------
+# Global 4N x 4N x (3N-2) layout (Algorithm 2: OutOrder, DodecantCoords).
+# --------------------------------------------------------------------------
+# Algorithm 2's output tables as printed (1-based dimension numbers; a
+# negative entry flips that output dimension after the permutation).
+OUT_ORDER = [(-2, -1, 3), (-1, 2, 3), (2, 1, 3), (1, -2, 3),
+             (2, 1, 3), (1, -2, 3), (-1, 2, 3), (-2, -1, 3),
+             (2, 1, 3), (-1, 2, 3), (1, -2, 3), (-2, -1, 3)]
+DODECANT_COORDS = [(1, 1), (1, 2), (2, 2), (2, 1),
+                   (0, 2), (0, 1), (3, 2), (3, 1),
+                   (2, 0), (1, 0), (2, 3), (1, 3)]
+
+
+def place_global(R: np.ndarray) -> np.ndarray:
+    """Algorithm 2's merge of the 12 dodecant outputs R[k][s1][s2][d]
+    (d in [0, 3N)) into one 4N x 4N x (3N-2) array: drop displacements 0 and 1
+    (always zero; the global array keeps 3N-2), permute the dodecant's
+    dimensions as abs(OutOrder[k]) (output dimension i takes input dimension
+    |OutOrder[k][i]|), flip the output dimensions with negative entries, and
+    store the block at (DodecantCoords[k][0] N, DodecantCoords[k][1] N).
+    The four unused blocks stay zero."""
+    N = R.shape[1]
+    G = np.zeros((4 * N, 4 * N, 3 * N - 2), dtype=R.dtype)
+    for k in range(12):
+        A = R[k][:, :, 2:]
+        order = OUT_ORDER[k]
+        A = np.transpose(A, [abs(o) - 1 for o in order])
+        for dim, o in enumerate(order):
+            if o < 0:
+                A = np.flip(A, axis=dim)
+        b0, b1 = DODECANT_COORDS[k]
+        G[b0 * N:(b0 + 1) * N, b1 * N:(b1 + 1) * N, :] = A
+    return G
+
+
+def planes_global(f: np.ndarray) -> np.ndarray:
+    """The 3D DRT of a cube in Algorithm 2's global layout (int32)."""
+    return place_global(planes_forward(f))
+
+
+def dodecant_frame_axes(N: int, k: int) -> list:
+    """For frame axes x', y', z' of dodecant k: (original axis, +1 or -1)."""
+    lib = _load()
+    o = lib.drto_dodecant_src(N, k, 0, 0, 0)
+    strides = {N * N: 0, N: 1, 1: 2}
+    out = []
+    for v in [(1, 0, 0), (0, 1, 0), (0, 0, 1)]:
+        d = lib.drto_dodecant_src(N, k, *v) - o
+        out.append((strides[abs(d)], 1 if d > 0 else -1))
+    return out
+
+
+# --------------------------------------------------------------------------
 # Dense operator (tiny N) for condition numbers (Table "condNumber").
 # --------------------------------------------------------------------------
 def planes_matrix(N: int) -> np.ndarray:

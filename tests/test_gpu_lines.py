@@ -123,3 +123,21 @@ def test_lines_adjoint_errors(drt):
         drt.lines_adjoint(torch.zeros((12, N, N, 2 * N, 2 * N), dtype=torch.float32, device="cuda"))
     with pytest.raises(ValueError):
         drt.lines_adjoint(torch.zeros((11, N, N, 2 * N, 2 * N), dtype=torch.int32, device="cuda"))
+
+
+def test_ray_in_noise_threshold_and_backproject(drt):
+    """Section 4.1's example: a ray under white noise of twice its amplitude is
+    the largest coefficient of its sector's DJT; backprojecting only that
+    coefficient gives back exactly the ray's voxels, and with the 16 largest
+    (the ray's neighbours share voxels with it) most of them."""
+    from paper_2501_13664_gb300 import demos
+
+    line = (37, 90, 150, 140)
+    res = demos.ray_in_noise(N=128, amplitude=16, noise=32, top=1, line=line)
+    assert res["line_voxels"] == 128  # the line crosses the whole cube
+    assert res["peak"] == line
+    assert demos.recovered_fraction(res) == 1.0
+    res = demos.ray_in_noise(N=128, amplitude=16, noise=32, top=16, line=line)
+    assert res["peak"] == line
+    assert res["line_coefficient"] > res["largest_other"]
+    assert demos.recovered_fraction(res) >= 0.8

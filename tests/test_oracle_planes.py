@@ -151,3 +151,90 @@ def test_condition_number_regression(oracle_mod, N, want):
     24.1062 (N=8); the 12-dodecant operator as defined gives the values below,
     recorded as a regression only."""
     assert abs(oracle_mod.cond_number(N) - want) < 1e-3
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 2's global 4N x 4N x (3N-2) layout.
+# ---------------------------------------------------------------------------
+def _global_normals(oracle_mod, N):
+    """Continuous plane normal, in the original axes, of every (I, J) cell of
+    the global layout: the dodecant-frame plane z' = s1/(N-1) x' + s2/(N-1) y'
+    has normal (-s1/(N-1), -s2/(N-1), 1); the frame's axis map carries it back.
+    The cells are placed with the same OutOrder / DodecantCoords steps."""
+    nrm = np.zeros((4 * N, 4 * N, 3))
+    used = np.zeros((4 * N, 4 * N), dtype=bool)
+    s1, s2 = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    frame = np.stack([-s1 / (N - 1), -s2 / (N - 1), np.ones((N, N))], axis=-1)
+    for k in range(12):
+        orig = np.zeros_like(frame)
+        for i, (axis, sign) in enumerate(oracle_mod.dodecant_frame_axes(N, k)):
+            orig[..., axis] = sign * frame[..., i]
+        order = oracle_mod.OUT_ORDER[k]
+        A = np.transpose(orig, [abs(order[0]) - 1, abs(order[1]) - 1, 2])
+        for dim in (0, 1):
+            if order[dim] < 0:
+                A = np.flip(A, axis=dim)
+        b0, b1 = oracle_mod.DODECANT_COORDS[k]
+        nrm[b0 * N:(b0 + 1) * N, b1 * N:(b1 + 1) * N] = A
+        used[b0 * N:(b0 + 1) * N, b1 * N:(b1 + 1) * N] = True
+    return nrm, used
+
+
+@pytest.mark.parametrize("N", [8, 16, 32])
+def test_global_layout_is_continuous(oracle_mod, N):
+    """With the InOrder reading, OutOrder and DodecantCoords as printed tile the
+    sphere of plane orientations continuously: neighbouring cells of the
+    4N x 4N layout, across every block seam too, differ by at most one slope
+    step (as unoriented plane normals), and exactly 12 blocks are used."""
+    nrm, used = _global_normals(oracle_mod, N)
+    assert used.sum() == 12 * N * N
+    u = np.zeros_like(nrm)
+    u[used] = nrm[used] / np.linalg.norm(nrm[used], axis=-1, keepdims=True)
+    step = np.arctan(1.0 / (N - 1))
+
+    def angle(p, q):
+        return np.arccos(np.clip(np.abs((p * q).sum(-1)), 0.0, 1.0))
+
+    h = angle(u[:, :-1], u[:, 1:])[used[:, :-1] & used[:, 1:]]
+    v = angle(u[:-1], u[1:])[used[:-1] & used[1:]]
+    assert max(h.max(), v.max()) <= step * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("N", [4, 8, 16])
+def test_global_layout_blocks(oracle_mod, N):
+    """Every used (I, J) column holds one plane family: its sum over the 3N-2
+    displacements is the volume's mass; unused blocks are zero; each cell is
+    its dodecant's plane sum by the definition (spot checks)."""
+    f = synth.random_int32((N, N, N), 90 + N, 0, 256)
+    G = oracle_mod.planes_global(f).astype(np.int64)
+    assert G.shape == (4 * N, 4 * N, 3 * N - 2)
+    _, used = _global_normals(oracle_mod, N)
+    np.testing.assert_array_equal(G.sum(axis=2)[used], int(f.astype(np.int64).sum()))
+    np.testing.assert_array_equal(G[~used], 0)
+    rng = np.random.default_rng(N)
+    for _ in range(20):
+        k = int(rng.integers(12))
+        s1, s2 = (int(x) for x in rng.integers(0, N, 2))
+        d = int(rng.integers(2, 3 * N))
+        order = oracle_mod.OUT_ORDER[k]
+        idx = [s1, s2]
+        out = [idx[abs(order[0]) - 1], idx[abs(order[1]) - 1]]
+        out = [N - 1 - out[i] if order[i] < 0 else out[i] for i in (0, 1)]
+        b0, b1 = oracle_mod.DODECANT_COORDS[k]
+        assert G[b0 * N + out[0], b1 * N + out[1], d - 2] == oracle_mod.planes_cell_global(f, k, s1, s2, d)
+
+
+def test_global_layout_continuity_catches_a_flipped_block(oracle_mod, monkeypatch):
+    """The continuity pin is sharp: one flipped or transposed block breaks it."""
+    N = 16
+    step = np.arctan(1.0 / (N - 1))
+    for k, bad in [(5, (-1, -2, 3)), (0, (-1, -2, 3)), (9, (2, 1, 3))]:
+        table = list(oracle_mod.OUT_ORDER)
+        table[k] = bad
+        monkeypatch.setattr(oracle_mod, "OUT_ORDER", table)
+        nrm, used = _global_normals(oracle_mod, N)
+        u = np.zeros_like(nrm)
+        u[used] = nrm[used] / np.linalg.norm(nrm[used], axis=-1, keepdims=True)
+        h = np.arccos(np.clip(np.abs((u[:, :-1] * u[:, 1:]).sum(-1)), 0, 1))[used[:, :-1] & used[:, 1:]]
+        v = np.arccos(np.clip(np.abs((u[:-1] * u[1:]).sum(-1)), 0, 1))[used[:-1] & used[1:]]
+        assert max(h.max(), v.max()) > 2 * step
