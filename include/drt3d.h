@@ -132,6 +132,20 @@ drt3d_status drt3d_planes_forward(const drt3d_plan* plan, const void* d_in, void
                                   uint32_t dodecant_mask, void* d_ws, size_t ws_bytes,
                                   cudaStream_t stream);
 
+/* The 3D DRT of a cube in Algorithm 2's global layout: all 12 dodecants merged
+ * into one 4N x 4N x (3N-2) array.  Dodecant k's output R_k[s1][s2][d] goes to
+ * block DodecantCoords[k] (N x N cells), its two slope dimensions permuted by
+ * |OutOrder[k]| and reversed where OutOrder[k] is negative (OutOrder and
+ * DodecantCoords as printed in Algorithm 2), displacement d at index d - 2
+ * (d = 0, 1 are always zero and are dropped; d is not reversed).  The four
+ * corner blocks, which no dodecant uses, are zeroed.  The remap is done by the
+ * last pass's stores; nothing is copied.
+ *   d_out : 16 N^2 (3N - 2) int32 (or float for F32 plans), overwritten.
+ *   d_ws, ws_bytes: as drt3d_planes_forward with all 12 dodecants.
+ * N >= 4.  Errors: INVALID_ARG, SIZE, ALIGN, WORKSPACE, CUDA. */
+drt3d_status drt3d_planes_forward_global(const drt3d_plan* plan, const void* d_in, void* d_out, void* d_ws,
+                                         size_t ws_bytes, cudaStream_t stream);
+
 /* Adjoint (backprojection) of drt3d_planes_forward (Section 5.1, stage loop
  * reversed with eq.(invmap3Dsummation); reads below d = 0 are zero):
  *   d_vol = sum over selected k, in increasing k, of g_k^T(A_k^T d_cot[k]).

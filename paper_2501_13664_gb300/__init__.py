@@ -229,6 +229,22 @@ def planes_forward(vol: torch.Tensor, dodecants=ALL, out: torch.Tensor | None = 
     return out
 
 
+def planes_forward_global(vol: torch.Tensor, out: torch.Tensor | None = None,
+                          workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """All 12 dodecants in Algorithm 2's global 4N x 4N x (3N-2) layout."""
+    vol_d, host = _to_device(vol)
+    N = _vol_check(vol_d)
+    plan = get_plan(N, vol_d.dtype)
+    if out is None:
+        odt = torch.float32 if vol_d.dtype == torch.float32 else torch.int32
+        out = torch.empty((4 * N, 4 * N, 3 * N - 2), dtype=odt, device=vol_d.device)
+    ws = workspace if workspace is not None else plan.workspace("planes_forward")
+    _abi.check(plan._lib.drt3d_planes_forward_global(plan.handle, vol_d.data_ptr(), out.data_ptr(),
+                                                     ws.data_ptr(), ws.numel(), _stream()),
+               "drt3d_planes_forward_global")
+    return out.to("cpu") if host else out
+
+
 def planes_adjoint(cot: torch.Tensor, dodecants=ALL, out: torch.Tensor | None = None,
                    workspace: torch.Tensor | None = None) -> torch.Tensor:
     """Backprojection (Section 5.1), summed over the selected dodecants."""

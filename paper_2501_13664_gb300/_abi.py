@@ -32,6 +32,7 @@ SIGNATURES = {
     "drt3d_planes_inverse": (I, [P, P, I, P, P, SZ, P]),
     "djt3d_lines_forward": (I, [P, P, P, U32, P, SZ, P]),
     "djt3d_lines_adjoint": (I, [P, P, P, U32, P, SZ, P]),
+    "drt3d_planes_forward_global": (I, [P, P, P, P, SZ, P]),
     "drt3d_get_device_error": (I, [P, P]),
     "drt3d_status_string": (ctypes.c_char_p, [I]),
     "drt3d_set_profiling": (I, [P, I]),

@@ -391,8 +391,35 @@ drt3d_status drt3d_workspace_bytes(const drt3d_plan* P, int op, size_t* bytes) {
     return DRT3D_ERR_INVALID_ARG;
 }
 
-drt3d_status drt3d_planes_forward(const drt3d_plan* P, const void* d_in, void* d_out, uint32_t mask,
-                                  void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+// Algorithm 2's output tables (OutOrder with 1-based dimension numbers, a
+// negative entry flipping that output dimension after the permutation, and
+// DodecantCoords), as printed in the paper.
+static const int kOutOrder[12][2] = {{-2, -1}, {-1, 2}, {2, 1}, {1, -2}, {2, 1}, {1, -2},
+                                     {-1, 2}, {-2, -1}, {2, 1}, {-1, 2}, {1, -2}, {-2, -1}};
+static const int kDodecantCoords[12][2] = {{1, 1}, {1, 2}, {2, 2}, {2, 1}, {0, 2}, {0, 1},
+                                           {3, 2}, {3, 1}, {2, 0}, {1, 0}, {2, 3}, {1, 3}};
+
+// Row of dodecant k's (s1, s2) in the 4N x 4N global array, as
+// g0 + s1 g1 + s2 g2: output dimension i takes (s1, s2)[|OutOrder[k][i]| - 1],
+// reversed when the entry is negative, inside block DodecantCoords[k].
+static void global_row_map(int N, int k, FusedSlot& fs) {
+    long long c[2];
+    long long a[2][2];  // a[i][j]: coefficient of (s1, s2)[j] in output index i
+    for (int i = 0; i < 2; ++i) {
+        const int e = kOutOrder[k][i];
+        const int src = (e < 0 ? -e : e) - 1;
+        a[i][0] = a[i][1] = 0;
+        a[i][src] = e < 0 ? -1 : 1;
+        c[i] = e < 0 ? N - 1 : 0;
+    }
+    const long long W = 4LL * N;
+    fs.g0 = ((long long)kDodecantCoords[k][0] * N + c[0]) * W + (long long)kDodecantCoords[k][1] * N + c[1];
+    fs.g1 = (int)(a[0][0] * W + a[1][0]);
+    fs.g2 = (int)(a[0][1] * W + a[1][1]);
+}
+
+static drt3d_status planes_forward_impl(const drt3d_plan* P, const void* d_in, void* d_out, uint32_t mask,
+                                        void* d_ws, size_t ws_bytes, cudaStream_t stream, bool global) {
     if (!P || !d_in || !d_out) return DRT3D_ERR_INVALID_ARG;
     if (mask == 0 || (mask & ~DRT3D_ALL_DODECANTS)) return DRT3D_ERR_INVALID_ARG;
     if (!aligned16(d_in) || !aligned16(d_out) || !aligned16(d_ws)) return DRT3D_ERR_ALIGN;
@@ -419,8 +446,9 @@ drt3d_status drt3d_planes_forward(const drt3d_plan* P, const void* d_in, void* d
             fs.map = dodecant_affine(N, k);
             fused_ingest_mode(N, fs.map, fs);
             fs.in = (p == 0) ? d_in : ((p & 1) ? (const void*)bufA : (const void*)bufB);
-            fs.out = ps.final_ ? (void*)(static_cast<char*>(d_out) + (size_t)i * out_block)
+            fs.out = ps.final_ ? (void*)(static_cast<char*>(d_out) + (global ? 0 : (size_t)i * out_block))
                                : ((p & 1) ? (void*)bufB : (void*)bufA);
+            if (global) global_row_map(N, k, fs);
             ++i;
         }
         L.m0 = ps.m0;
@@ -431,6 +459,7 @@ drt3d_status drt3d_planes_forward(const drt3d_plan* P, const void* d_in, void* d
         const long long per_axis = 1LL << (P->n - ps.G);
         L.ctas = per_axis * per_axis * L.ntiles;
         L.vec_store = (ps.out.pitch % 4 == 0) && (ps.out.base % 4 == 0) && (3 * N) % 4 == 0;
+        L.global_layout = (global && ps.final_) ? 1 : 0;
         char nm[40];
         std::snprintf(nm, sizeof nm, "planes_fused G=%d m0=%d", ps.G, ps.m0);
         prof_begin(P, stream, nm, nslots * fused_pass_bytes(P, ps));
@@ -443,6 +472,28 @@ drt3d_status drt3d_planes_forward(const drt3d_plan* P, const void* d_in, void* d
         prof_end(P, stream);
     }
     return DRT3D_OK;
+}
+
+drt3d_status drt3d_planes_forward(const drt3d_plan* P, const void* d_in, void* d_out, uint32_t mask,
+                                  void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+    return planes_forward_impl(P, d_in, d_out, mask, d_ws, ws_bytes, stream, false);
+}
+
+drt3d_status drt3d_planes_forward_global(const drt3d_plan* P, const void* d_in, void* d_out, void* d_ws,
+                                         size_t ws_bytes, cudaStream_t stream) {
+    if (!P || !d_in || !d_out) return DRT3D_ERR_INVALID_ARG;
+    if (P->N < 4) return DRT3D_ERR_SIZE;
+    if (!aligned16(d_out)) return DRT3D_ERR_ALIGN;
+    const int N = P->N;
+    const size_t gp = (size_t)(3 * N - 2) * 4;  // bytes per global row
+    // The four corner blocks hold no dodecant: zero them.
+    for (int b0 : {0, 3})
+        for (int b1 : {0, 3}) {
+            char* blk = static_cast<char*>(d_out) + ((size_t)b0 * N * 4 * N + (size_t)b1 * N) * gp;
+            if (cudaMemset2DAsync(blk, 4 * (size_t)N * gp, 0, (size_t)N * gp, N, stream) != cudaSuccess)
+                return DRT3D_ERR_CUDA;
+        }
+    return planes_forward_impl(P, d_in, d_out, DRT3D_ALL_DODECANTS, d_ws, ws_bytes, stream, true);
 }
 
 drt3d_status drt3d_planes_adjoint(const drt3d_plan* P, const void* d_cot, void* d_vol, uint32_t mask,

@@ -205,8 +205,36 @@ __device__ __forceinline__ void store_rows(const FusedLaunch& L, const FusedSlot
     if (p0 >= L.V || d >= L.dmax) return;
     const int m0 = L.m0;
     const int o1 = t1 + (sg1 << G) + (wq1 << (m0 + G));
-    TOut* out = static_cast<TOut*>(sp.out) + (d - L.gout.base);
     const long long orow0 = (long long)o1 * rs1 + (long long)((sg2 << G) + (wq2 << (m0 + G))) * rs2;
+    if constexpr (sizeof(TOut) == 4) {
+        if (L.global_layout) {
+            // Algorithm 2's array: row g0 + s1 g1 + s2 g2, pitch 3N - 2, the
+            // displacement index shifted down by 2 (rows 0 and 1 are dropped).
+            const int gp = 3 * L.N - 2;
+            TOut* gout = static_cast<TOut*>(sp.out);
+#pragma unroll
+            for (int t2 = 0; t2 < R; ++t2) {
+                const long long r = orow0 + (long long)t2 * rs2;
+                const long long grow = sp.g0 + (r >> L.n) * sp.g1 + (r & (L.N - 1)) * sp.g2;
+                TOut* dst = gout + grow * gp + (d - 2);
+                TOut e[K];
+#pragma unroll
+                for (int i = 0; i < K; ++i) e[i] = (TOut)v[t2][i];
+                if (d >= 2) {
+                    uint2 w0, w1;
+                    memcpy(&w0, e, 8);
+                    memcpy(&w1, e + 2, 8);
+                    st_global(reinterpret_cast<uint2*>(dst), w0);
+                    st_global(reinterpret_cast<uint2*>(dst + 2), w1);
+                } else {
+                    st_global(dst + 2, e[2]);
+                    st_global(dst + 3, e[3]);
+                }
+            }
+            return;
+        }
+    }
+    TOut* out = static_cast<TOut*>(sp.out) + (d - L.gout.base);
     const long long rstride = (long long)rs2 * L.gout.pitch;
     TOut* dst = out + orow0 * L.gout.pitch;
     if (L.vec_store) {

@@ -123,6 +123,10 @@ struct FusedSlot {
     int swap;     // 1: phase 1 runs along the second frame axis (y')
     int mode;     // kIngest* (first pass only)
     int reverse;  // the contiguous axis runs backwards in memory
+    // Global layout (last pass only): output row (s1, s2) goes to row
+    // g0 + s1 g1 + s2 g2 of the 4N x 4N x (3N - 2) array.
+    long long g0;
+    int g1, g2;
 };
 
 struct FusedLaunch {
@@ -136,6 +140,7 @@ struct FusedLaunch {
     long long ctas;  // CTAs per slot
     int vec_store;   // output rows allow aligned vector stores
     int* status;     // device status word (time-outs of staged loads), may be null
+    int global_layout;  // last pass writes Algorithm 2's 4N x 4N x (3N - 2) array
 };
 
 // One fused pass: G stages of eq.(map3D) (both axes).

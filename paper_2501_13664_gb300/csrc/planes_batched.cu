@@ -99,6 +99,7 @@ __device__ __forceinline__ void run_g(const FusedLaunch& Lg, int slot, unsigned 
     L.ctas = Lg.ctas;
     L.vec_store = Lg.vec_store;
     L.status = status;
+    L.global_layout = 0;
     const FusedSlot sp = Lg.slot[slot];
     // one item = one unit: all its displacement tiles
     const unsigned nt = (unsigned)L.ntiles;
