@@ -22,6 +22,11 @@ John transforms" (arXiv 2501.13664):
 * ``lines_brute``           -- eq.(3DfDJT), Section 4.1
 * ``lines_alg3``            -- Algorithm 3 with eq.(map3DJ)
 * ``lines_forward``         -- the twelve line sectors of Section 4.1
+* ``drt2d_brute``           -- the 2D DRT of lines by its definition
+                               (stage n of eq.(our2Dfm)), Section 2.1
+* ``drt2d_map2d``           -- the 2D stage recursion eq.(map2D)
+* ``drt2d_forward``         -- the four quadrants of Section 2.2 (axes
+                               swapped and/or flipped), batched
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms,
 invariants and brute force; ``cond_number`` (Table "condNumber") is the one
@@ -91,6 +96,9 @@ def _load():
             "drto_lines_alg3_i32": (I, [I, P, P]),
             "drto_lines_adjoint_brute_i64": (None, [I, P, P]),
             "drto_lines_adjoint_i32": (I, [I, P, P]),
+            "drto_drt2d_brute_i64": (None, [I, P, P]),
+            "drto_drt2d_map2d_i32": (I, [I, P, P]),
+            "drto_drt2d_map2d_f64": (I, [I, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -482,3 +490,79 @@ def cond_number(N: int) -> float:
     the paper's printed values are not reproduced by this operator."""
     s = np.linalg.svd(planes_matrix(N), compute_uv=False)
     return float(s[0] / s[-1])
+
+
+# --------------------------------------------------------------------------
+# 2D DRT of lines (Section 2.1, eq.(map2D)) and its four quadrants.
+# --------------------------------------------------------------------------
+N_QUADRANTS = 4
+
+
+def _square(f: np.ndarray) -> int:
+    if f.ndim != 2 or f.shape[0] != f.shape[1]:
+        raise ValueError("expected an N x N image")
+    _check_N(f.shape[0])
+    return f.shape[0]
+
+
+def drt2d_brute(f: np.ndarray) -> np.ndarray:
+    """R[s][d] = sum_u f(u, l_s(u) + d - N) by scatter, int64 or float64, (N, 2N)."""
+    N = _square(f)
+    if np.issubdtype(f.dtype, np.floating):
+        # exact enough in float64 for the sizes tested: evaluate the same
+        # scatter with numpy on the lline table
+        L = lline_table(N)
+        R = np.zeros((N, 2 * N), dtype=np.float64)
+        y = np.arange(N)
+        for s in range(N):
+            for u in range(N):
+                np.add.at(R[s], y - L[s, u] + N, f[u].astype(np.float64))
+        return R
+    ff = np.ascontiguousarray(f, dtype=np.int64)
+    R = np.empty((N, 2 * N), dtype=np.int64)
+    _load().drto_drt2d_brute_i64(N, _ptr(ff), _ptr(R))
+    return R
+
+
+def drt2d_map2d(f: np.ndarray) -> np.ndarray:
+    """The n stages of eq.(map2D) on one image: int32 wrapping for integer
+    input, float64 for floating input, shape (N, 2N)."""
+    N = _square(f)
+    lib = _load()
+    if np.issubdtype(f.dtype, np.floating):
+        ff = np.ascontiguousarray(f, dtype=np.float64)
+        R = np.empty((N, 2 * N), dtype=np.float64)
+        rc = lib.drto_drt2d_map2d_f64(N, _ptr(ff), _ptr(R))
+    else:
+        ff = np.ascontiguousarray(f.astype(np.int32, copy=False))
+        R = np.empty((N, 2 * N), dtype=np.int32)
+        rc = lib.drto_drt2d_map2d_i32(N, _ptr(ff), _ptr(R))
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    return R
+
+
+def quadrant_image(f: np.ndarray, q: int) -> np.ndarray:
+    """Image seen by quadrant q (Section 2.2: the basic quadrant reused on
+    swapped and/or flipped copies of the input).  Bit 1 of q swaps the axes
+    (lines driven by y instead of x), bit 0 reverses the other axis:
+    f_q(u, y) = f(u, y), f(u, N-1-y), f(y, u), f(N-1-y, u) for q = 0..3."""
+    if not 0 <= q < N_QUADRANTS:
+        raise ValueError("quadrant out of range")
+    g = f.T if q & 2 else f
+    return g[:, ::-1] if q & 1 else g
+
+
+def drt2d_forward(imgs: np.ndarray, quadrants=range(N_QUADRANTS), exact: str = "map2d") -> np.ndarray:
+    """2D DRT of a batch of images (B, N, N) for the given quadrants:
+    out[b][i] is quadrant ``quadrants[i]`` of image b, shape (B, nq, N, 2N)
+    (int32 wrapping for integer input, float64 for floating input)."""
+    if imgs.ndim != 3:
+        raise ValueError("expected (B, N, N) images")
+    qs = list(quadrants)
+    fn = drt2d_brute if exact == "brute" else drt2d_map2d
+    out = [[fn(np.ascontiguousarray(quadrant_image(im, q))) for q in qs] for im in imgs]
+    res = np.array(out)
+    if exact == "brute" and not np.issubdtype(imgs.dtype, np.floating):
+        res = res.astype(np.int32, casting="unsafe")
+    return res

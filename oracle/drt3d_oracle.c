@@ -570,3 +570,65 @@ int drto_lines_adjoint_i32(int N, const int32_t* Jbar_, int32_t* gbar_) {
     free(fm); free(fn);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* 2D DRT of lines, the basic quadrant (Section 2.1).  An image f[u][y],      */
+/* N x N; output R[s][d], d in [0, 2N), the storage index with the image      */
+/* embedded at d in [N, 2N), so the line is y = l_s(u) + d - N.               */
+/* ------------------------------------------------------------------------ */
+
+/* Definition (the stage-n form of eq.(our2Dfm)): brute-force scatter of     */
+/* every pixel onto the one displacement it lies on for each slope.          */
+/*   R[s][d] = sum_u f(u, l_s(u) + d - N)                                     */
+void drto_drt2d_brute_i64(int N, const int64_t* f, int64_t* R) {
+    const int n = ilog2(N), W = 2 * N;
+    memset(R, 0, sizeof(int64_t) * (size_t)N * W);
+    for (int s = 0; s < N; ++s)
+        for (int u = 0; u < N; ++u) {
+            const int64_t l = drto_lline(n, s, u);
+            for (int y = 0; y < N; ++y) R[(int64_t)s * W + (y - l + N)] += f[(int64_t)u * N + y];
+        }
+}
+
+/* Stage recursion eq.(map2D).  The partial transform of stage m is stored   */
+/* as fm[sigma][v][d]: sigma = lambda of the m slope bits, v = lambda of the  */
+/* n - m position bits still to be summed, flattened to row                   */
+/* sigma * 2^(n-m) + v.  Stage 0 is the image (sigma empty, v = u), stage n   */
+/* is R (v empty).  One stage prepends the slope bit s_{n-m-1} as the new     */
+/* least significant bit (S = 2 sigma + s_{n-m-1}) and consumes the lowest    */
+/* position bit v_m:                                                          */
+/*   f^{m+1}(S | V | d) = f^m(sigma | 2V | d)                                 */
+/*                      + f^m(sigma | 2V + 1 | d + s_{n-m-1} + sigma),        */
+/* and s_{n-m-1} + sigma = floor((S + 1) / 2).  Reads past 2N are zero.       */
+#define DRTO_MAP2D_BODY(T)                                                          \
+    const int n = ilog2(N), W = 2 * N;                                              \
+    const size_t cells = (size_t)N * W;                                             \
+    T* fm = (T*)calloc(cells, sizeof(T));                                           \
+    T* fn = (T*)calloc(cells, sizeof(T));                                           \
+    if (!fm || !fn) { free(fm); free(fn); return -1; }                              \
+    for (int u = 0; u < N; ++u)                                                     \
+        for (int y = 0; y < N; ++y) fm[(size_t)u * W + N + y] = (T)f[(size_t)u * N + y]; \
+    for (int m = 0; m < n; ++m) {                                                   \
+        const int Vn = 1 << (n - m - 1);  /* position values after the stage */    \
+        for (int S = 0; S < (2 << m); ++S)                                          \
+            for (int V = 0; V < Vn; ++V) {                                          \
+                const int sigma = S >> 1, sh = (S + 1) >> 1;                        \
+                const T* lo = fm + ((size_t)sigma * (2 * Vn) + 2 * V) * W;          \
+                const T* hi = fm + ((size_t)sigma * (2 * Vn) + 2 * V + 1) * W;      \
+                T* out = fn + ((size_t)S * Vn + V) * W;                             \
+                for (int d = 0; d < W; ++d)                                         \
+                    out[d] = lo[d] + ((d + sh < W) ? hi[d + sh] : (T)0);            \
+            }                                                                       \
+        T* t = fm; fm = fn; fn = t;                                                 \
+    }                                                                               \
+    memcpy(R, fm, cells * sizeof(T));                                               \
+    free(fm); free(fn);                                                             \
+    return 0;
+
+int drto_drt2d_map2d_i32(int N, const int32_t* f, int32_t* R_) {
+    uint32_t* R = (uint32_t*)R_;
+    DRTO_MAP2D_BODY(uint32_t)
+}
+int drto_drt2d_map2d_f64(int N, const double* f, double* R) {
+    DRTO_MAP2D_BODY(double)
+}
