@@ -431,6 +431,8 @@ def run_ours(args):
         torch.cuda.empty_cache()
         line["lsq_c5"] = bench_lsq(drt3d, synth, dev)
         torch.cuda.empty_cache()
+        line["drt2d_images"] = bench_drt2d(drt3d, synth, dev)
+        torch.cuda.empty_cache()
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         pool, workers = oracle_pool(f_np)
@@ -544,6 +546,38 @@ def bench_lines(drt3d, synth, dev) -> dict:
             "adjoint_ms": ta, "adjoint_floor_gbs": afloor / (ta / 1000) / 1e9,
             "workload": "N=128 int16 uniform 0..1023 + 32 lines, 12 sectors, int32 out; adjoint of that "
                         "transform back to an int32 volume"}
+
+
+def bench_drt2d(drt3d, synth, dev) -> dict:
+    """The 2D DRT by-product: 512 uint8 images of 256^2, four quadrants, int32
+    out (1.07 GB written per call, larger than L2)."""
+    import torch
+
+    N, B = 256, 512
+    imgs = torch.from_numpy(synth.images_2d(N, B)).to(dev)
+    out = torch.empty((B, 4, N, 2 * N), dtype=torch.int32, device=dev)
+    plan = drt3d.get_plan(N, torch.uint8)
+    run = lambda: drt3d.drt2d_forward(imgs, range(4), out=out)  # noqa: E731
+    for _ in range(3):
+        run()
+    t = sorted(_event_ms(run, 7))[3]
+    plan.set_profiling(True)
+    run()
+    torch.cuda.synchronize()
+    passes = {}
+    for name, ms, by in plan.profiled_launches():
+        e = passes.setdefault(name, {"launches": 0, "ms": 0.0, "algo_bytes": 0.0})
+        e["launches"] += 1
+        e["ms"] += ms
+        e["algo_bytes"] += by
+    plan.set_profiling(False)
+    for e in passes.values():
+        e["gbs"] = e["algo_bytes"] / (e["ms"] / 1000) / 1e9
+    floor = B * N * N * 1.0 + B * 4.0 * N * 2 * N * 4
+    del out
+    return {"ms": t, "images_per_s": B / (t / 1000), "floor_gbs": floor / (t / 1000) / 1e9, "passes": passes,
+            "workload": "512 uint8 images 256x256 (5 % pixels 1..255 + 4 lines of 255 each), four quadrants, "
+                        "int32 out; chunks of images sized so intermediates stay in L2"}
 
 
 def bench_lsq(drt3d, synth, dev) -> dict:

@@ -90,6 +90,7 @@ typedef enum drt3d_op {
 
 #define DRT3D_ALL_DODECANTS 0xFFFu
 #define DRT3D_ALL_SECTORS 0xFFFu
+#define DRT2D_ALL_QUADRANTS 0xFu
 
 typedef struct drt3d_plan drt3d_plan;
 
@@ -193,6 +194,29 @@ drt3d_status djt3d_lines_forward(const drt3d_plan* plan, const void* d_in, int32
  * ALIGN, WORKSPACE, CUDA. */
 drt3d_status djt3d_lines_adjoint(const drt3d_plan* plan, const int32_t* d_cot, int32_t* d_vol,
                                  uint32_t sector_mask, void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/* 2D DRT of lines (Section 2.1: the stage recursion eq.(map2D); the four
+ * quadrants of Section 2.2), for a batch of images, using the plan's N and
+ * input dtype.
+ *   d_img : B images f[b][x][y], N x N each, of the plan's dtype.
+ *   d_out : B blocks of popcount(quadrant_mask) arrays R[q][s][d] of N x 2N
+ *           int32 (float32 for an F32 plan), quadrants in increasing order,
+ *           overwritten.  The cell sums the digital line
+ *           y' = l_s(u) + d - N over u of quadrant q's view f_q(u, y') of the
+ *           image: f(u, y'), f(u, N-1-y'), f(y', u), f(N-1-y', u) for
+ *           q = 0..3 (bit 1 swaps the axes, bit 0 reverses the other one).
+ *           d = 0 is always zero.
+ *   quadrant_mask : bits 0..3, non-zero.
+ *   d_ws, ws_bytes: workspace for the intermediate stages of one chunk of
+ *           images; drt2d_workspace_bytes() gives a size that keeps a chunk's
+ *           intermediates near 32 MiB.  Any size that holds one image works
+ *           (images are processed in chunks of what fits); N <= 16 needs none.
+ *   B = 0 is a no-op.  Integer input is exact in wrapping int32; float input
+ *   is summed in float32 in a fixed order.  Errors: INVALID_ARG, ALIGN,
+ *   WORKSPACE, CUDA. */
+drt3d_status drt2d_forward(const drt3d_plan* plan, const void* d_img, int B, void* d_out, uint32_t quadrant_mask,
+                           void* d_ws, size_t ws_bytes, cudaStream_t stream);
+drt3d_status drt2d_workspace_bytes(const drt3d_plan* plan, int B, uint32_t quadrant_mask, size_t* bytes);
 
 /* Stage-fusion schedule of the planes forward: the n = log2 N stages of
  * eq.(map3D) run in `ngroups` passes of G[0], G[1], ... stages on both axes

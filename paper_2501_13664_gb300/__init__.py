@@ -13,6 +13,8 @@ copied to the current CUDA device and the result copied back):
 * ``planes_adjoint(cot, dodecants)``   -> (N, N, N)
 * ``planes_inverse(R_k, dodecant)``    -> (N, N, N) int32
 * ``lines_forward(vol, sectors)``      -> (k, N, N, 2N, 2N) int32
+* ``lines_adjoint(cot, sectors)``      -> (N, N, N) int32
+* ``drt2d_forward(imgs, quadrants)``   -> (B, q, N, 2N) int32 / float32
 * ``PlanesTransform``                  -- torch.autograd.Function (float32)
 """
 from __future__ import annotations
@@ -333,6 +335,48 @@ def lines_adjoint(cot: torch.Tensor, sectors=ALL, out: torch.Tensor | None = Non
     _abi.check(plan._lib.djt3d_lines_adjoint(plan.handle, cot_d.data_ptr(), out.data_ptr(), m,
                                              ws.data_ptr(), ws.numel(), _stream()),
                "djt3d_lines_adjoint")
+    return out.to("cpu") if host else out
+
+
+def _quad_mask(sel) -> int:
+    if isinstance(sel, int):
+        m = sel
+    else:
+        m = 0
+        for q in sel:
+            if not 0 <= int(q) < 4:
+                raise ValueError(f"quadrant index out of range: {q}")
+            m |= 1 << int(q)
+    if m <= 0 or m > 0xF:
+        raise ValueError(f"bad quadrant mask {m:#x}")
+    return m
+
+
+def drt2d_forward(imgs: torch.Tensor, quadrants=range(4), out: torch.Tensor | None = None,
+                  workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """2D DRT of lines (eq.(map2D)) of a batch of N x N images (B, N, N) or
+    one image (N, N), over the selected quadrants: (B, q, N, 2N)."""
+    img_d, host = _to_device(imgs)
+    single = img_d.dim() == 2
+    if single:
+        img_d = img_d.unsqueeze(0)
+    if img_d.dim() != 3 or img_d.shape[1] != img_d.shape[2]:
+        raise ValueError(f"expected (B, N, N) images, got {tuple(imgs.shape)}")
+    B, N = int(img_d.shape[0]), int(img_d.shape[1])
+    m = _quad_mask(quadrants)
+    plan = get_plan(N, img_d.dtype)
+    odt = torch.float32 if img_d.dtype == torch.float32 else torch.int32
+    if out is None:
+        out = torch.empty((B, _count(m), N, 2 * N), dtype=odt, device=img_d.device)
+    if workspace is None:
+        v = ctypes.c_size_t()
+        _abi.check(plan._lib.drt2d_workspace_bytes(plan.handle, B, m, ctypes.byref(v)), "drt2d_workspace_bytes")
+        workspace = torch.empty(max(16, int(v.value)), dtype=torch.uint8, device=img_d.device)
+    _abi.check(plan._lib.drt2d_forward(plan.handle, img_d.data_ptr(), B, out.data_ptr(), m,
+                                       workspace.data_ptr(), workspace.numel(), _stream()),
+               "drt2d_forward")
+    if single:
+        out = out[0]
     return out.to("cpu") if host else out
 
 

@@ -33,6 +33,8 @@ SIGNATURES = {
     "djt3d_lines_forward": (I, [P, P, P, U32, P, SZ, P]),
     "djt3d_lines_adjoint": (I, [P, P, P, U32, P, SZ, P]),
     "drt3d_planes_forward_global": (I, [P, P, P, P, SZ, P]),
+    "drt2d_forward": (I, [P, P, I, P, U32, P, SZ, P]),
+    "drt2d_workspace_bytes": (I, [P, I, U32, ctypes.POINTER(SZ)]),
     "drt3d_get_device_error": (I, [P, P]),
     "drt3d_status_string": (ctypes.c_char_p, [I]),
     "drt3d_set_profiling": (I, [P, I]),

@@ -298,6 +298,42 @@ static double fused_pass_bytes(const drt3d_plan* P, const FusedPass& ps) {
     return in_b + out_b;
 }
 
+// 2D DRT of lines: the n stages split into ceil(n / 4) near-equal groups; the
+// rows after m stages are stored over d in [base, 2N) (nothing below
+// N + 1 - 2^m can be non-zero), base rounded down to 4, pitch up to 4.
+static int drt2d_groups(int n, int* G) {
+    const int ng = (n + 3) / 4;
+    for (int g = 0; g < ng; ++g) G[g] = n / ng + (g < n % ng ? 1 : 0);
+    return ng;
+}
+static int drt2d_base(int N, int m) { return m >= ilog2(N) ? 0 : (N + 1 - (1 << m)) & ~3; }
+static int drt2d_pitch(int N, int m) { return (int)align_up((size_t)(2 * N - drt2d_base(N, m)), 4); }
+// Bytes of one (image, quadrant) slot of the largest intermediate, and how
+// many intermediates are live at once.
+static size_t drt2d_slot_bytes(int N, int* nbuf) {
+    int G[4];
+    const int ng = drt2d_groups(ilog2(N), G);
+    size_t mx = 0;
+    for (int g = 0, m = 0; g + 1 < ng; ++g) {
+        m += G[g];
+        mx = std::max(mx, (size_t)N * drt2d_pitch(N, m) * 4);
+    }
+    *nbuf = ng <= 1 ? 0 : (ng == 2 ? 1 : 2);
+    return mx;
+}
+// Images per chunk for a workspace of `ws` bytes (0 if none fits).
+static long long drt2d_chunk(int N, int nq, int B, size_t ws) {
+    int nbuf;
+    const size_t slot = drt2d_slot_bytes(N, &nbuf);
+    if (nbuf == 0) return std::min<long long>(B, 65535 / nq);
+    const long long c = (long long)(ws / ((size_t)nbuf * nq * slot));
+    return std::min<long long>(std::min<long long>(c, B), 65535 / nq);
+}
+// Default workspace: chunks whose intermediates stay near 32 MiB, so that a
+// pass's output is still in L2 when the next pass reads it.
+constexpr size_t kDrt2dChunkTarget = 32u << 20;
+static int quad_count(uint32_t m) { return ((m >> 0) & 1) + ((m >> 1) & 1) + ((m >> 2) & 1) + ((m >> 3) & 1); }
+
 }  // namespace drt3d
 
 using namespace drt3d;
@@ -734,6 +770,77 @@ drt3d_status djt3d_lines_adjoint(const drt3d_plan* P, const int32_t* d_cot, int3
     prof_begin(P, stream, "djt_adj_gather", (double)nslots * N * N * N * 4 + (double)N * N * N * 4);
     if (launch_djt_adj_gather(Gt, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
     prof_end(P, stream);
+    return DRT3D_OK;
+}
+
+drt3d_status drt2d_workspace_bytes(const drt3d_plan* P, int B, uint32_t qmask, size_t* bytes) {
+    if (!P || !bytes || B < 0 || qmask == 0 || (qmask & ~DRT2D_ALL_QUADRANTS)) return DRT3D_ERR_INVALID_ARG;
+    int nbuf;
+    const size_t slot = drt2d_slot_bytes(P->N, &nbuf);
+    const int nq = quad_count(qmask);
+    if (nbuf == 0 || B == 0) {
+        *bytes = 0;
+        return DRT3D_OK;
+    }
+    const long long per_image = (long long)nbuf * nq * slot;
+    long long c = std::max<long long>(1, (long long)(kDrt2dChunkTarget / (size_t)per_image));
+    c = std::min<long long>(std::min<long long>(c, B), 65535 / nq);
+    *bytes = (size_t)(c * per_image);
+    return DRT3D_OK;
+}
+
+drt3d_status drt2d_forward(const drt3d_plan* P, const void* d_img, int B, void* d_out, uint32_t qmask, void* d_ws,
+                           size_t ws_bytes, cudaStream_t stream) {
+    if (!P || B < 0 || qmask == 0 || (qmask & ~DRT2D_ALL_QUADRANTS)) return DRT3D_ERR_INVALID_ARG;
+    if (B == 0) return DRT3D_OK;
+    if (!d_img || !d_out) return DRT3D_ERR_INVALID_ARG;
+    if (!aligned16(d_img) || !aligned16(d_out) || !aligned16(d_ws)) return DRT3D_ERR_ALIGN;
+    const int N = P->N, n = P->n;
+    const int nq = quad_count(qmask);
+    int nbuf;
+    const size_t slot_bytes = drt2d_slot_bytes(N, &nbuf);
+    const long long chunk = drt2d_chunk(N, nq, B, ws_bytes);
+    if (nbuf > 0 && (!d_ws || chunk < 1)) return DRT3D_ERR_WORKSPACE;
+    int G[4];
+    const int ng = drt2d_groups(n, G);
+    const int esz = P->dtype == DRT3D_U8 ? 1 : P->dtype == DRT3D_I16 ? 2 : 4;
+    Drt2dLaunch L{};
+    L.N = N;
+    L.n = n;
+    L.nq = nq;
+    L.vec_ingest = N >= 4 && (N * esz) % 16 == 0;
+    for (int q = 0, i = 0; q < 4; ++q)
+        if ((qmask >> q) & 1) L.quad[i++] = q;
+    const long long out_per_image = (long long)nq * N * 2 * N;  // elements
+    char* bufs[2] = {static_cast<char*>(d_ws), static_cast<char*>(d_ws) + (size_t)chunk * nq * slot_bytes};
+    for (long long b0 = 0; b0 < B; b0 += chunk) {
+        const int nimg = (int)std::min<long long>(chunk, B - b0);
+        const int nslots = nimg * nq;
+        for (int g = 0, m = 0; g < ng; m += G[g], ++g) {
+            const bool first = g == 0, last = g + 1 == ng;
+            L.m0 = m;
+            L.in = first ? static_cast<const void*>(static_cast<const char*>(d_img) + (size_t)b0 * N * N * esz)
+                         : static_cast<const void*>(bufs[(g - 1) & 1]);
+            L.in_base = drt2d_base(N, m);
+            L.in_pitch = drt2d_pitch(N, m);
+            L.in_slot = (long long)slot_bytes / 4;
+            L.out = last ? static_cast<void*>(static_cast<char*>(d_out) + (size_t)b0 * out_per_image * 4)
+                         : static_cast<void*>(bufs[g & 1]);
+            L.out_base = last ? 0 : drt2d_base(N, m + G[g]);
+            L.out_pitch = last ? 2 * N : drt2d_pitch(N, m + G[g]);
+            L.out_slot = last ? (long long)N * 2 * N : (long long)slot_bytes / 4;
+            L.V = drt2d_tile_valid(G[g]);
+            L.ntiles = (2 * N - L.out_base + L.V - 1) / L.V;
+            L.warps = (1LL << (n - G[g])) * L.ntiles;
+            char nm[40];
+            std::snprintf(nm, sizeof nm, "drt2d_pass G=%d m0=%d", G[g], m);
+            const double in_b = first ? (double)N * N * esz : (double)N * (2 * N - L.in_base) * 4;
+            const double out_b = (double)N * (2 * N - L.out_base) * 4;
+            prof_begin(P, stream, nm, (first ? (double)nimg * in_b : (double)nslots * in_b) + nslots * out_b);
+            if (launch_drt2d_pass(L, G[g], P->dtype, first, nslots, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+            prof_end(P, stream);
+        }
+    }
     return DRT3D_OK;
 }
 

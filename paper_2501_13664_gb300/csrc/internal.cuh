@@ -226,6 +226,26 @@ int djt_adj_lanes_k();
 cudaError_t launch_djt_pass(const DjtLaunch& L, int G, int K, drt3d_dtype in_dtype, bool ingest, bool final_,
                             int nslots, cudaStream_t s);
 
+// One pass of the 2D DRT of lines (drt2d.cu).  Slot i of the launch is
+// (image i / nq, quadrant quad[i % nq]) of one chunk of images.
+struct Drt2dLaunch {
+    const void* in;          // images (first pass) or the previous pass's rows
+    void* out;               // rows of this pass, or the final (s, d) arrays
+    int N, n, m0;            // stages before the pass
+    int in_base, in_pitch;   // input rows: d in [in_base, 2N)
+    long long in_slot;       // elements per input slot
+    int out_base, out_pitch;
+    long long out_slot;
+    int V, ntiles;           // valid displacements per warp tile, tiles per row
+    long long warps;         // warps per slot
+    int nq;
+    int quad[4];
+    int vec_ingest;          // first pass: image rows allow 16-byte vector loads
+};
+int drt2d_tile_valid(int G);
+cudaError_t launch_drt2d_pass(const Drt2dLaunch& L, int G, drt3d_dtype in_dtype, bool ingest, int nslots,
+                              cudaStream_t s);
+
 int fused_valid(int G);  // valid displacements per CTA tile of a G-stage fused pass
 cudaError_t launch_planes_fused(const FusedLaunch& L, int G, ElemKind in_kind, ElemKind out_kind,
                                 bool ingest, int nslots, cudaStream_t s);

@@ -21,6 +21,11 @@ Workloads (numpy ``default_rng(seed)`` throughout):
                      256:6 shuffled (seed 4), each drawn like ``c2_volume``
                      with seed 4 + i.
 * ``c5_batch``    -- 8 x 128^3 float32, standard normal (seed 5).
+* ``images_2d``   -- B x N x N uint8 images (B=512, N=256 by default): zeros,
+                     5 % of pixels at uniform positions set to uniform 1..255,
+                     then 4 straight lines of value 255 per image at random
+                     slope and intercept (seed 6); the by-product 2D DRT's
+                     batch (the paper gives no 2D workload of its own).
 """
 from __future__ import annotations
 
@@ -152,3 +157,26 @@ def random_float(shape, seed: int) -> np.ndarray:
     """Standard normal float32."""
     rng = np.random.default_rng(seed)
     return rng.standard_normal(size=shape, dtype=np.float32)
+
+
+def images_2d(N: int = 256, batch: int = 512, seed: int = 6, lines: int = 4) -> np.ndarray:
+    """``batch`` sparse uint8 images with ``lines`` straight lines of 255 each."""
+    rng = np.random.default_rng(seed)
+    f = np.zeros((batch, N * N), dtype=np.uint8)
+    k = max(1, (N * N) // 20)
+    for b in range(batch):
+        pos = rng.choice(N * N, size=k, replace=False)
+        f[b, pos] = rng.integers(1, 256, size=k, dtype=np.int64).astype(np.uint8)
+    f = f.reshape(batch, N, N)
+    u = np.arange(N)
+    for b in range(batch):
+        for _ in range(lines):
+            slope = int(rng.integers(-(N - 1), N))
+            icpt = int(rng.integers(0, N))
+            v = icpt + _raster(u, slope, N)
+            ok = (v >= 0) & (v < N)
+            if rng.integers(0, 2):
+                f[b, u[ok], v[ok]] = 255
+            else:
+                f[b, v[ok], u[ok]] = 255
+    return f
