@@ -27,6 +27,8 @@ John transforms" (arXiv 2501.13664):
 * ``drt2d_map2d``           -- the 2D stage recursion eq.(map2D)
 * ``drt2d_forward``         -- the four quadrants of Section 2.2 (axes
                                swapped and/or flipped), batched
+* ``press`` (submodule)     -- Section 5.2's iterative inverse: adjoint +
+                               high-pass filter h, multigrid with P and S
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms,
 invariants and brute force; ``cond_number`` (Table "condNumber") is the one
