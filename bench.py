@@ -433,6 +433,8 @@ def run_ours(args):
         torch.cuda.empty_cache()
         line["drt2d_images"] = bench_drt2d(drt3d, synth, dev)
         torch.cuda.empty_cache()
+        line["press_inverse"] = bench_press(drt3d, synth, dev)
+        torch.cuda.empty_cache()
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         pool, workers = oracle_pool(f_np)
@@ -578,6 +580,32 @@ def bench_drt2d(drt3d, synth, dev) -> dict:
     return {"ms": t, "images_per_s": B / (t / 1000), "floor_gbs": floor / (t / 1000) / 1e9, "passes": passes,
             "workload": "512 uint8 images 256x256 (5 % pixels 1..255 + 4 lines of 255 each), four quadrants, "
                         "int32 out; chunks of images sized so intermediates stay in L2"}
+
+
+def bench_press(drt3d, synth, dev) -> dict:
+    """Section 5.2's iterative inverse on a 128^3 float32 phantom (the size
+    of the paper's MRI inversions): error after 5, 10 and 20 iterations and
+    the time of 10."""
+    import torch
+
+    N = 128
+    f = torch.from_numpy(synth.phantom(N)).to(dev)
+    R = drt3d.planes_forward(f)
+    steps = drt3d.press_step_sizes(N)
+    plan = drt3d.get_plan(N, torch.float32)
+    ws = plan.workspace("planes_press")
+    out = torch.empty_like(f)
+    rng = float(f.max() - f.min())
+
+    def nrmsd(k):
+        drt3d.planes_press_inverse(R, k, 2, steps, out=out, workspace=ws)
+        return float(torch.sqrt(torch.mean((out - f) ** 2)) / rng)
+
+    errs = {k: nrmsd(k) for k in (1, 5, 10, 20)}
+    run = lambda: drt3d.planes_press_inverse(R, 10, 2, steps, out=out, workspace=ws)  # noqa: E731
+    t = sorted(_event_ms(run, 3))[1]
+    return {"ms_10_iterations": t, "ms_per_iteration": t / 10, "nrmsd": errs, "smooth": 2, "step_factor": 1.5,
+            "workload": "128^3 float32 phantom (6 solid ellipsoids), all 12 dodecants, multigrid down to N=1"}
 
 
 def bench_lsq(drt3d, synth, dev) -> dict:

@@ -85,7 +85,8 @@ typedef enum drt3d_op {
     DRT3D_OP_PLANES_ADJOINT = 1,
     DRT3D_OP_PLANES_INVERSE = 2,
     DRT3D_OP_LINES_FORWARD = 3,
-    DRT3D_OP_LINES_ADJOINT = 4
+    DRT3D_OP_LINES_ADJOINT = 4,
+    DRT3D_OP_PLANES_PRESS = 5
 } drt3d_op;
 
 #define DRT3D_ALL_DODECANTS 0xFFFu
@@ -194,6 +195,42 @@ drt3d_status djt3d_lines_forward(const drt3d_plan* plan, const void* d_in, int32
  * ALIGN, WORKSPACE, CUDA. */
 drt3d_status djt3d_lines_adjoint(const drt3d_plan* plan, const int32_t* d_cot, int32_t* d_vol,
                                  uint32_t sector_mask, void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Iterative inverse of the planes transform (Section 5.2: the adjoint
+ * followed by the high-pass filter h as an approximate inverse, improved
+ * iteratively with a multigrid of prolongations P and restrictions S).
+ * With A the twelve-dodecant forward and B_L r = steps[l] * h (*) A_L^T r at
+ * size L = 2^l (h with mirrored borders: an outside neighbour takes the
+ * nearest voxel inside):
+ *   f_0 = 0;  f_{k+1} = f_k + M_N(d_R - A f_k)  for k < iterations, where
+ *   M_N(r): r_N = r, r_{L/2} = S r_L down to L = 1; x_1 = mean over the
+ *   twelve dodecants of r_1(0, 0, 2) (exact at N = 1); then for L = 2 .. N:
+ *   x_L = P x_{L/2} and `smooth` times x_L += B_L (r_L - A_L x_L).
+ *   S: r_{L/2}(s1, s2, d) = (r_L(2s1, 2s2, 2d) + r_L(2s1, 2s2, 2d + 1)) / 8;
+ *   P: x_L(i, j, k) = x_{L/2}(i/2, j/2, k/2).
+ *   d_R   : 12 blocks of N*N*3N float32 (all dodecants, drt3d_planes_forward's
+ *           layout).
+ *   d_vol : N^3 float32, overwritten with f_iterations (zero for 0 iterations).
+ *   steps : host array of n + 1 floats, steps[l] > 0 for l = 1..n (entry 0
+ *           unused); steps[l] = factor / drt3d_press_spectral_radius(l) with
+ *           factor < 2 makes each smoothing step contract.
+ *   d_ws, ws_bytes: >= drt3d_workspace_bytes(PLANES_PRESS) (about 450 N^3
+ *           bytes plus the forward's workspace).
+ * Plan dtype must be F32.  The coarser levels' plans are created (host
+ * memory only) on first use and released with the plan.  Errors:
+ * INVALID_ARG, DTYPE, ALIGN, WORKSPACE, NO_MEMORY, CUDA. */
+drt3d_status drt3d_planes_press_inverse(const drt3d_plan* plan, const float* d_R, float* d_vol, int iterations,
+                                        int smooth, const float* steps, void* d_ws, size_t ws_bytes,
+                                        cudaStream_t stream);
+
+/* Spectral radius of h (*) A_L^T A_L at size L = 2^level (1 <= level <= n)
+ * by `iterations` steps of the power iteration from d_start (L^3 float32,
+ * non-zero): x = start / ||start||, then y = h (*) A^T A x, x = y / ||y||;
+ * *lambda = ||y|| of the last step.  Synchronises `stream` to return the
+ * value.  Same plan and workspace as drt3d_planes_press_inverse.  Errors:
+ * INVALID_ARG, DTYPE, ALIGN, WORKSPACE, NO_MEMORY, CUDA. */
+drt3d_status drt3d_press_spectral_radius(const drt3d_plan* plan, int level, const float* d_start, int iterations,
+                                         double* lambda, void* d_ws, size_t ws_bytes, cudaStream_t stream);
 
 /* 2D DRT of lines (Section 2.1: the stage recursion eq.(map2D); the four
  * quadrants of Section 2.2), for a batch of images, using the plan's N and

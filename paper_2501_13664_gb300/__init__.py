@@ -15,6 +15,8 @@ copied to the current CUDA device and the result copied back):
 * ``lines_forward(vol, sectors)``      -> (k, N, N, 2N, 2N) int32
 * ``lines_adjoint(cot, sectors)``      -> (N, N, N) int32
 * ``drt2d_forward(imgs, quadrants)``   -> (B, q, N, 2N) int32 / float32
+* ``planes_press_inverse(R, iters)``   -> (N, N, N) float32, Section 5.2's
+                                          iterative (multigrid) inverse
 * ``PlanesTransform``                  -- torch.autograd.Function (float32)
 """
 from __future__ import annotations
@@ -377,6 +379,63 @@ def drt2d_forward(imgs: torch.Tensor, quadrants=range(4), out: torch.Tensor | No
                "drt2d_forward")
     if single:
         out = out[0]
+    return out.to("cpu") if host else out
+
+
+_press_steps_cache: dict = {}
+
+
+def press_step_sizes(N: int, factor: float = 1.5, iterations: int = 30, seed: int = 0) -> list:
+    """Step sizes of the iterative inverse: [0, c_1, ..., c_n] with
+    c_l = factor / (spectral radius of h * A^T A at size 2^l), each radius
+    from ``iterations`` power-iteration steps on the GPU from a seeded
+    normal start vector.  Cached per device and arguments."""
+    dev = torch.cuda.current_device()
+    key = (dev, int(N), float(factor), int(iterations), int(seed))
+    if key in _press_steps_cache:
+        return list(_press_steps_cache[key])
+    plan = get_plan(N, torch.float32)
+    ws = plan.workspace("planes_press")
+    n = int(N).bit_length() - 1
+    steps = [0.0]
+    for level in range(1, n + 1):
+        L = 1 << level
+        g = torch.Generator(device=f"cuda:{dev}").manual_seed(seed + L)
+        start = torch.randn((L, L, L), generator=g, device=f"cuda:{dev}", dtype=torch.float32)
+        lam = ctypes.c_double()
+        _abi.check(plan._lib.drt3d_press_spectral_radius(plan.handle, level, start.data_ptr(), iterations,
+                                                          ctypes.byref(lam), ws.data_ptr(), ws.numel(), _stream()),
+                   "drt3d_press_spectral_radius")
+        steps.append(factor / lam.value)
+    _press_steps_cache[key] = tuple(steps)
+    return steps
+
+
+def planes_press_inverse(R: torch.Tensor, iterations: int = 10, smooth: int = 2, steps=None,
+                         out: torch.Tensor | None = None, workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """Iterative inverse of the twelve-dodecant planes transform (Section 5.2):
+    ``R`` is (12, N, N, 3N) float32; returns the (N, N, N) float32 volume after
+    ``iterations`` multigrid improvements with ``smooth`` smoothing steps per
+    level.  ``steps`` defaults to ``press_step_sizes(N)``."""
+    R_d, host = _to_device(R)
+    if R_d.dtype != torch.float32 or R_d.dim() != 4 or R_d.shape[0] != 12:
+        raise ValueError("expected a (12, N, N, 3N) float32 transform")
+    N = int(R_d.shape[1])
+    if tuple(R_d.shape) != (12, N, N, 3 * N):
+        raise ValueError(f"expected (12, N, N, 3N), got {tuple(R_d.shape)}")
+    plan = get_plan(N, torch.float32)
+    if steps is None:
+        steps = press_step_sizes(N)
+    n = N.bit_length() - 1
+    if len(steps) != n + 1:
+        raise ValueError(f"need {n + 1} step sizes (entry 0 unused)")
+    arr = (ctypes.c_float * (n + 1))(*[float(c) for c in steps])
+    if out is None:
+        out = torch.empty((N, N, N), dtype=torch.float32, device=R_d.device)
+    ws = workspace if workspace is not None else plan.workspace("planes_press")
+    _abi.check(plan._lib.drt3d_planes_press_inverse(plan.handle, R_d.data_ptr(), out.data_ptr(), int(iterations),
+                                                    int(smooth), arr, ws.data_ptr(), ws.numel(), _stream()),
+               "drt3d_planes_press_inverse")
     return out.to("cpu") if host else out
 
 

@@ -34,6 +34,8 @@ SIGNATURES = {
     "djt3d_lines_adjoint": (I, [P, P, P, U32, P, SZ, P]),
     "drt3d_planes_forward_global": (I, [P, P, P, P, SZ, P]),
     "drt2d_forward": (I, [P, P, I, P, U32, P, SZ, P]),
+    "drt3d_planes_press_inverse": (I, [P, P, P, I, I, ctypes.POINTER(ctypes.c_float), P, SZ, P]),
+    "drt3d_press_spectral_radius": (I, [P, I, P, I, ctypes.POINTER(ctypes.c_double), P, SZ, P]),
     "drt2d_workspace_bytes": (I, [P, I, U32, ctypes.POINTER(SZ)]),
     "drt3d_get_device_error": (I, [P, P]),
     "drt3d_status_string": (ctypes.c_char_p, [I]),
@@ -63,7 +65,8 @@ STATUS = {
     11: "DRT3D_ERR_SCRATCH_LIMIT",
 }
 DTYPES = {"u8": 0, "i16": 1, "i32": 2, "f32": 3}
-OPS = {"planes_forward": 0, "planes_adjoint": 1, "planes_inverse": 2, "lines_forward": 3, "lines_adjoint": 4}
+OPS = {"planes_forward": 0, "planes_adjoint": 1, "planes_inverse": 2, "lines_forward": 3, "lines_adjoint": 4,
+       "planes_press": 5}
 
 
 class DRT3DError(RuntimeError):

@@ -388,9 +388,13 @@ drt3d_status drt3d_plan_create(drt3d_plan** plan, int N, drt3d_dtype in_dtype, u
 
 drt3d_status drt3d_plan_destroy(drt3d_plan* plan) {
     if (!plan) return DRT3D_OK;
+    for (drt3d_plan*& lp : plan->levels) {
+        drt3d_plan_destroy(lp);
+        lp = nullptr;
+    }
     if (plan->prof.events_made)
         for (int i = 0; i < 2 * kMaxLaunch; ++i) cudaEventDestroy(plan->prof.ev[i]);
-    if (plan->d_status) cudaFree(plan->d_status);
+    if (plan->d_status && !plan->borrowed_status) cudaFree(plan->d_status);
     delete plan;
     return DRT3D_OK;
 }
@@ -405,6 +409,66 @@ drt3d_status drt3d_lines_out_shape(const drt3d_plan* P, int64_t dims[5]) {
     if (!P || !dims) return DRT3D_ERR_INVALID_ARG;
     dims[0] = 12; dims[1] = P->N; dims[2] = P->N; dims[3] = 2 * (int64_t)P->N; dims[4] = 2 * (int64_t)P->N;
     return DRT3D_OK;
+}
+
+// --------------------------------------------------------------------------
+// Iterative inverse (Section 5.2): float32 plans of the coarser sizes and the
+// workspace layout.
+// --------------------------------------------------------------------------
+static drt3d_plan* level_plan(const drt3d_plan* P, int l) {
+    if (l == P->n) return const_cast<drt3d_plan*>(P);
+    if (!P->levels[l]) {
+        drt3d_plan* q = new (std::nothrow) drt3d_plan();
+        if (!q) return nullptr;
+        q->N = 1 << l;
+        q->n = l;
+        q->dtype = DRT3D_F32;
+        q->flags = 0;
+        q->device = P->device;
+        q->d_status = P->d_status;
+        q->borrowed_status = true;
+        q->planes = make_planes_schedule(q->N);
+        q->fused = make_fused_schedule(q->N, DRT3D_F32);
+        P->levels[l] = q;
+    }
+    return P->levels[l];
+}
+
+struct PressLayout {
+    size_t r[11];  // restricted residual of each level 2^l (r[n]: top-level residual)
+    size_t t;      // A x of the level being smoothed
+    size_t x[11];  // solution of each level
+    size_t b;      // backprojection
+    size_t partial, norm;
+    size_t tws;    // forward / adjoint workspace
+    size_t tws_bytes;
+    size_t total;
+};
+static PressLayout press_layout(const drt3d_plan* P) {
+    PressLayout Lo{};
+    const int N = P->N, n = P->n;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += align_up(bytes, 256);
+        return o;
+    };
+    for (int l = 0; l <= n; ++l) {
+        const size_t L = (size_t)1 << l;
+        Lo.r[l] = take(12 * L * L * 3 * L * 4);
+    }
+    Lo.t = take((size_t)12 * N * N * 3 * N * 4);
+    for (int l = 0; l <= n; ++l) {
+        const size_t L = (size_t)1 << l;
+        Lo.x[l] = take(L * L * L * 4);
+    }
+    Lo.b = take((size_t)N * N * N * 4);
+    Lo.partial = take(kPressNormParts * sizeof(double));
+    Lo.norm = take(sizeof(double));
+    Lo.tws_bytes = std::max((size_t)kMaxSlots * 2 * P->fused.buf_bytes, (size_t)kMaxSlots * 2 * planes_buf_bytes(P));
+    Lo.tws = take(Lo.tws_bytes);
+    Lo.total = off;
+    return Lo;
 }
 
 drt3d_status drt3d_workspace_bytes(const drt3d_plan* P, int op, size_t* bytes) {
@@ -422,6 +486,10 @@ drt3d_status drt3d_workspace_bytes(const drt3d_plan* P, int op, size_t* bytes) {
         return DRT3D_OK;
     case DRT3D_OP_LINES_ADJOINT:
         *bytes = (size_t)kMaxSlots * djt_adj_slot_bytes(P->N);
+        return DRT3D_OK;
+    case DRT3D_OP_PLANES_PRESS:
+        if (P->dtype != DRT3D_F32) return DRT3D_ERR_DTYPE;
+        *bytes = press_layout(P).total;
         return DRT3D_OK;
     }
     return DRT3D_ERR_INVALID_ARG;
@@ -770,6 +838,110 @@ drt3d_status djt3d_lines_adjoint(const drt3d_plan* P, const int32_t* d_cot, int3
     prof_begin(P, stream, "djt_adj_gather", (double)nslots * N * N * N * 4 + (double)N * N * N * 4);
     if (launch_djt_adj_gather(Gt, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
     prof_end(P, stream);
+    return DRT3D_OK;
+}
+
+// One smoothing step at level l: x += c * h (*) A^T (r - A x).
+static drt3d_status press_smooth(const drt3d_plan* P, int l, const float* r, float* x, float c, char* ws,
+                                 const PressLayout& Lo, cudaStream_t stream) {
+    const drt3d_plan* lp = level_plan(P, l);
+    if (!lp) return DRT3D_ERR_NO_MEMORY;
+    const int L = 1 << l;
+    float* t = reinterpret_cast<float*>(ws + Lo.t);
+    float* b = reinterpret_cast<float*>(ws + Lo.b);
+    drt3d_status st = planes_forward_impl(lp, x, t, DRT3D_ALL_DODECANTS, ws + Lo.tws, Lo.tws_bytes, stream, false);
+    if (st != DRT3D_OK) return st;
+    if (launch_press_residual(r, t, 12LL * L * L * 3 * L, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+    st = drt3d_planes_adjoint(lp, t, b, DRT3D_ALL_DODECANTS, ws + Lo.tws, Lo.tws_bytes, stream);
+    if (st != DRT3D_OK) return st;
+    if (launch_press_filter(b, x, L, c, true, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+    return DRT3D_OK;
+}
+
+static bool press_args_ok(const drt3d_plan* P, void* d_ws, size_t ws_bytes, drt3d_status* err) {
+    if (P->dtype != DRT3D_F32) { *err = DRT3D_ERR_DTYPE; return false; }
+    if (!aligned16(d_ws)) { *err = DRT3D_ERR_ALIGN; return false; }
+    if (!d_ws || ws_bytes < press_layout(P).total) { *err = DRT3D_ERR_WORKSPACE; return false; }
+    for (int l = 1; l < P->n; ++l)
+        if (!level_plan(P, l)) { *err = DRT3D_ERR_NO_MEMORY; return false; }
+    return true;
+}
+
+drt3d_status drt3d_planes_press_inverse(const drt3d_plan* P, const float* d_R, float* d_vol, int iterations,
+                                        int smooth, const float* steps, void* d_ws, size_t ws_bytes,
+                                        cudaStream_t stream) {
+    if (!P || !d_R || !d_vol || !steps || iterations < 0 || smooth < 1) return DRT3D_ERR_INVALID_ARG;
+    if (!aligned16(d_R) || !aligned16(d_vol)) return DRT3D_ERR_ALIGN;
+    drt3d_status st;
+    if (!press_args_ok(P, d_ws, ws_bytes, &st)) return st;
+    for (int l = 1; l <= P->n; ++l)
+        if (!(steps[l] > 0.f)) return DRT3D_ERR_INVALID_ARG;
+    const int N = P->N, n = P->n;
+    const long long vox = (long long)N * N * N;
+    const PressLayout Lo = press_layout(P);
+    char* ws = static_cast<char*>(d_ws);
+    auto fbuf = [&](size_t off) { return reinterpret_cast<float*>(ws + off); };
+    if (cudaMemsetAsync(d_vol, 0, (size_t)vox * 4, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+    for (int it = 0; it < iterations; ++it) {
+        // residual of the current solution (the data itself for f_0 = 0)
+        const float* rN = d_R;
+        if (it > 0) {
+            st = planes_forward_impl(P, d_vol, fbuf(Lo.r[n]), DRT3D_ALL_DODECANTS, ws + Lo.tws, Lo.tws_bytes,
+                                     stream, false);
+            if (st != DRT3D_OK) return st;
+            if (launch_press_residual(d_R, fbuf(Lo.r[n]), 12LL * N * N * 3 * N, stream) != cudaSuccess)
+                return DRT3D_ERR_CUDA;
+            rN = fbuf(Lo.r[n]);
+        }
+        // restrict down to N = 1 and solve there exactly
+        for (int l = n - 1; l >= 0; --l)
+            if (launch_press_restrict(l == n - 1 ? rN : fbuf(Lo.r[l + 1]), fbuf(Lo.r[l]), 1 << l, stream) !=
+                cudaSuccess)
+                return DRT3D_ERR_CUDA;
+        if (launch_press_coarsest(fbuf(Lo.r[0]), fbuf(Lo.x[0]), stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+        // prolongate and smooth level by level
+        for (int l = 1; l <= n; ++l) {
+            if (launch_press_prolong(fbuf(Lo.x[l - 1]), fbuf(Lo.x[l]), 1 << l, stream) != cudaSuccess)
+                return DRT3D_ERR_CUDA;
+            const float* rl = l == n ? rN : fbuf(Lo.r[l]);
+            for (int j = 0; j < smooth; ++j) {
+                st = press_smooth(P, l, rl, fbuf(Lo.x[l]), steps[l], ws, Lo, stream);
+                if (st != DRT3D_OK) return st;
+            }
+        }
+        if (launch_press_add(fbuf(Lo.x[n]), d_vol, vox, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+    }
+    return DRT3D_OK;
+}
+
+drt3d_status drt3d_press_spectral_radius(const drt3d_plan* P, int level, const float* d_start, int iterations,
+                                         double* lambda, void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!P || !d_start || !lambda || iterations < 1 || level < 1 || level > P->n) return DRT3D_ERR_INVALID_ARG;
+    if (!aligned16(d_start)) return DRT3D_ERR_ALIGN;
+    drt3d_status st;
+    if (!press_args_ok(P, d_ws, ws_bytes, &st)) return st;
+    const drt3d_plan* lp = level_plan(P, level);
+    const int L = 1 << level;
+    const long long vox = (long long)L * L * L;
+    const PressLayout Lo = press_layout(P);
+    char* ws = static_cast<char*>(d_ws);
+    float* x = reinterpret_cast<float*>(ws + Lo.x[level]);
+    float* t = reinterpret_cast<float*>(ws + Lo.t);
+    float* b = reinterpret_cast<float*>(ws + Lo.b);
+    double* partial = reinterpret_cast<double*>(ws + Lo.partial);
+    double* norm = reinterpret_cast<double*>(ws + Lo.norm);
+    if (launch_press_normalize(d_start, x, vox, partial, norm, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+    for (int it = 0; it < iterations; ++it) {
+        st = planes_forward_impl(lp, x, t, DRT3D_ALL_DODECANTS, ws + Lo.tws, Lo.tws_bytes, stream, false);
+        if (st != DRT3D_OK) return st;
+        st = drt3d_planes_adjoint(lp, t, b, DRT3D_ALL_DODECANTS, ws + Lo.tws, Lo.tws_bytes, stream);
+        if (st != DRT3D_OK) return st;
+        if (launch_press_filter(b, x, L, 1.f, false, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+        if (launch_press_normalize(x, x, vox, partial, norm, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+    }
+    if (cudaMemcpyAsync(lambda, norm, sizeof(double), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+        return DRT3D_ERR_CUDA;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return DRT3D_ERR_CUDA;
     return DRT3D_OK;
 }
 

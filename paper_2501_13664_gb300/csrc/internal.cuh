@@ -33,6 +33,8 @@
 
 #include <cuda.h>
 
+#include <algorithm>
+
 #include "drt3d.h"
 
 namespace drt3d {
@@ -246,6 +248,20 @@ int drt2d_tile_valid(int G);
 cudaError_t launch_drt2d_pass(const Drt2dLaunch& L, int G, drt3d_dtype in_dtype, bool ingest, int nslots,
                               cudaStream_t s);
 
+// Kernels of the iterative inverse (press.cu).  Volumes are N^3 float32,
+// transforms 12 dodecants of N x N x 3N float32.
+constexpr int kPressNormParts = 256;  // partial sums of one norm
+cudaError_t launch_press_filter(const float* b, float* y, int N, float c, bool accumulate, cudaStream_t s);
+cudaError_t launch_press_prolong(const float* xc, float* x, int N, cudaStream_t s);
+cudaError_t launch_press_restrict(const float* R, float* Rc, int Nc, cudaStream_t s);
+cudaError_t launch_press_coarsest(const float* R1, float* x1, cudaStream_t s);
+cudaError_t launch_press_residual(const float* r, float* t, long long n, cudaStream_t s);
+cudaError_t launch_press_add(const float* x, float* y, long long n, cudaStream_t s);
+// x = y / ||y||, ||y|| also stored (double) in *norm; partial holds
+// kPressNormParts doubles.
+cudaError_t launch_press_normalize(const float* y, float* x, long long n, double* partial, double* norm,
+                                   cudaStream_t s);
+
 int fused_valid(int G);  // valid displacements per CTA tile of a G-stage fused pass
 cudaError_t launch_planes_fused(const FusedLaunch& L, int G, ElemKind in_kind, ElemKind out_kind,
                                 bool ingest, int nslots, cudaStream_t s);
@@ -288,4 +304,9 @@ struct drt3d_plan {
     int* d_status;  // device status word (drt3d_status), 0 = OK
     drt3d::PlanesSchedule planes;  // one-axis passes (adjoint)
     drt3d::FusedSchedule fused;    // two-axis passes (forward)
+    // Float32 plans of the coarser sizes N/2, N/4, ..., 2 used by the
+    // iterative inverse, indexed by log2 of their size; host-only, created on
+    // first use, sharing this plan's status word.
+    mutable drt3d_plan* levels[11] = {};
+    bool borrowed_status = false;
 };

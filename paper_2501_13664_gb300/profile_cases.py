@@ -16,6 +16,11 @@ on the device at most.
                     sector 0 (268 MB of int32 out)
     batched-c4-n64  80 uint8 volumes with the N <= 64 sizes of the 96-volume
                     mixed batch, one persistent launch after one memset
+    lines-adj-n64   the lines-n64-s0 transform, then its adjoint (backprojection)
+    drt2d-n256      64 uint8 images of 256^2, 2D DRT over four quadrants
+                    (134 MB of int32 out)
+    press-n64       N=64 float32 phantom, two iterations of the multigrid
+                    inverse (step sizes from the power iteration first)
 """
 from __future__ import annotations
 
@@ -30,14 +35,16 @@ def _sched(s: str):
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("case", choices=["fused-n256-d1", "fused-n256", "inverse-n256", "lines-n64-s0", "batched-c4-n64"])
+    ap.add_argument("case", choices=["fused-n256-d1", "fused-n256", "inverse-n256", "lines-n64-s0", "batched-c4-n64",
+                                     "lines-adj-n64", "drt2d-n256", "press-n64"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--schedule", type=str, default="4,4", help="stage-fusion split of the N=256 planes cases")
     args = ap.parse_args(argv)
 
     import synth
 
-    from . import ALL, BatchPlan, get_plan, lines_forward, planes_forward, planes_inverse
+    from . import (ALL, BatchPlan, drt2d_forward, get_plan, lines_adjoint, lines_forward, planes_forward,
+                   planes_inverse, planes_press_inverse, press_step_sizes)
 
     dev = torch.device("cuda", 0)
     sched = _sched(args.schedule)
@@ -68,6 +75,36 @@ def main(argv=None) -> int:
         torch.cuda.synchronize()
         status = plan.device_error()
         print(f"{args.case}: reps={args.reps} schedule={plan.schedule()} status={status} sum={int(out[0].sum())}")
+    elif args.case == "lines-adj-n64":
+        N = 64
+        vol = torch.from_numpy(synth.c3_volume(N)).to(dev)
+        J = lines_forward(vol, [0])
+        plan = get_plan(N, torch.int32)
+        ws = plan.workspace("lines_adjoint")
+        back = torch.empty((N, N, N), dtype=torch.int32, device=dev)
+        for _ in range(args.reps):
+            lines_adjoint(J, [0], out=back, workspace=ws)
+        torch.cuda.synchronize()
+        status = plan.device_error()
+        print(f"{args.case}: reps={args.reps} status={status} sum={int(back.sum())}")
+    elif args.case == "drt2d-n256":
+        imgs = torch.from_numpy(synth.images_2d(256, 64)).to(dev)
+        out = torch.empty((64, 4, 256, 512), dtype=torch.int32, device=dev)
+        for _ in range(args.reps):
+            drt2d_forward(imgs, range(4), out=out)
+        torch.cuda.synchronize()
+        print(f"{args.case}: reps={args.reps} sum={int(out.sum())}")
+    elif args.case == "press-n64":
+        N = 64
+        f = torch.from_numpy(synth.phantom(N)).to(dev)
+        R = planes_forward(f)
+        steps = press_step_sizes(N)
+        out = torch.empty_like(f)
+        for _ in range(args.reps):
+            planes_press_inverse(R, 2, 2, steps, out=out)
+        torch.cuda.synchronize()
+        err = float(torch.sqrt(torch.mean((out - f) ** 2)) / (f.max() - f.min()))
+        print(f"{args.case}: reps={args.reps} nrmsd={err:.3e}")
     elif args.case == "lines-n64-s0":
         N = 64
         vol = torch.from_numpy(synth.c3_volume(N)).to(dev)

@@ -26,6 +26,10 @@ Workloads (numpy ``default_rng(seed)`` throughout):
                      then 4 straight lines of value 255 per image at random
                      slope and intercept (seed 6); the by-product 2D DRT's
                      batch (the paper gives no 2D workload of its own).
+* ``phantom``     -- N^3 float32 (N=128): a sum of 6 solid ellipsoids of
+                     random centre, semi-axes N/10..N/3 and intensity 0.2..1
+                     (seed 7); stands in for the paper's 128^3 head and spine
+                     MRI inversions (the scans themselves are not available).
 """
 from __future__ import annotations
 
@@ -180,3 +184,17 @@ def images_2d(N: int = 256, batch: int = 512, seed: int = 6, lines: int = 4) -> 
             else:
                 f[b, v[ok], u[ok]] = 255
     return f
+
+
+def phantom(N: int = 128, seed: int = 7, blobs: int = 6) -> np.ndarray:
+    """Sum of ``blobs`` solid ellipsoids, float32."""
+    rng = np.random.default_rng(seed)
+    x = (np.arange(N, dtype=np.float64) + 0.5) / N
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    f = np.zeros((N, N, N), dtype=np.float64)
+    for _ in range(blobs):
+        c = rng.uniform(0.3, 0.7, size=3)
+        a = rng.uniform(0.1, 1 / 3, size=3)
+        v = rng.uniform(0.2, 1.0)
+        f += v * ((((X - c[0]) / a[0]) ** 2 + ((Y - c[1]) / a[1]) ** 2 + ((Z - c[2]) / a[2]) ** 2) <= 1.0)
+    return f.astype(np.float32)
