@@ -18,7 +18,8 @@
 // unit's 2^G rows over the whole stored displacement range sit in shared
 // memory for the whole group, and each of the 2^(G-1) pairs of a stage is one
 // warp.  A lane holds a CH-displacement chunk of both rows of its pair in
-// registers (CH = 8..32, chosen so that one warp's chunks cover a row), forms
+// registers (CH = 8, 16 or 32; rows of more than 32 chunks are scanned in
+// segments of 32 chunks from the top, carrying the sum down), forms
 // nD = out_0 - out_1 and the chunk's suffix sums; one warp shuffle scan of the
 // chunk totals turns them into nT = -T.  lo = out_0 - nT goes back over out_0
 // and nT over out_1.  hi[e] = nT[e - S] is not copied: the slot records the
@@ -45,9 +46,10 @@ namespace {
 
 __host__ __device__ constexpr int inv_warps(int G) { return G >= 4 ? 8 : (1 << (G - 1)); }
 
-// Chunk width: the smallest of 8, 16, 24, 32 whose warp of chunks covers a
-// row of W displacements (32 beyond 1024: several segments).
-__host__ __device__ inline int inv_chunk_width(int W) { return W <= 256 ? 8 : W <= 512 ? 16 : W <= 768 ? 24 : 32; }
+// Chunk width: 8 up to 256 displacements (one segment), 16 up to 1024 (one
+// or two segments: smaller register and shared-memory footprint, so three
+// CTAs fit an SM, beats one segment of 24-wide chunks), 32 beyond.
+__host__ __device__ inline int inv_chunk_width(int W) { return W <= 256 ? 8 : W <= 1024 ? 16 : 32; }
 
 // Prefix chunks of a slot: the shifted copy of a half-stage with slope so
 // far S reads down to displacement -(S + 3); S < 2^(m0 + G - 1).
@@ -454,8 +456,8 @@ cudaError_t launch_inv_g(const InvLaunch& L, cudaStream_t s) {
     const int W = L.dmax - L.gin.base;
     switch (inv_chunk_width(W)) {
     case 8: return launch_inv_gc<G, 8, false>(L, s);
-    case 16: return launch_inv_gc<G, 16, false>(L, s);
-    case 24: return launch_inv_gc<G, 24, false>(L, s);
+    case 16:
+        return (W + 15) / 16 > 32 ? launch_inv_gc<G, 16, true>(L, s) : launch_inv_gc<G, 16, false>(L, s);
     default:
         return (W + 31) / 32 > 32 ? launch_inv_gc<G, 32, true>(L, s) : launch_inv_gc<G, 32, false>(L, s);
     }
