@@ -534,6 +534,7 @@ def bench_lines(drt3d, synth, dev) -> dict:
     run()
     t = sorted(_event_ms(run, 5))[2]
     floor = 12.0 * N * N * (2 * N) * (2 * N) * 4 + N ** 3 * 2
+    fwd_passes = profile_launches(plan, run)
     del ws
     # adjoint (backprojection) of the same 12 sectors, the transform as cotangent
     aplan = drt3d.get_plan(N, torch.int32)
@@ -543,11 +544,32 @@ def bench_lines(drt3d, synth, dev) -> dict:
     arun()
     ta = sorted(_event_ms(arun, 5))[2]
     afloor = 12.0 * N * N * (2 * N) * (2 * N) * 4 + N ** 3 * 4
+    adj_passes = profile_launches(aplan, arun)
     del out, aws
-    return {"ms": t, "sectors_per_s": 12 / (t / 1000), "floor_gbs": floor / (t / 1000) / 1e9,
-            "adjoint_ms": ta, "adjoint_floor_gbs": afloor / (ta / 1000) / 1e9,
+    return {"ms": t, "sectors_per_s": 12 / (t / 1000), "floor_gbs": floor / (t / 1000) / 1e9, "passes": fwd_passes,
+            "adjoint_ms": ta, "adjoint_floor_gbs": afloor / (ta / 1000) / 1e9, "adjoint_passes": adj_passes,
             "workload": "N=128 int16 uniform 0..1023 + 32 lines, 12 sectors, int32 out; adjoint of that "
                         "transform back to an int32 volume"}
+
+
+def profile_launches(plan, run) -> dict:
+    """Per-launch CUDA-event times of one call of `run` (the library's own
+    profiler on the launching stream), summed by launch name."""
+    import torch
+
+    plan.set_profiling(True)
+    run()
+    torch.cuda.synchronize()
+    passes = {}
+    for name, ms, by in plan.profiled_launches():
+        e = passes.setdefault(name, {"launches": 0, "ms": 0.0, "algo_bytes": 0.0})
+        e["launches"] += 1
+        e["ms"] += ms
+        e["algo_bytes"] += by
+    plan.set_profiling(False)
+    for e in passes.values():
+        e["gbs"] = e["algo_bytes"] / (e["ms"] / 1000) / 1e9 if e["ms"] > 0 else None
+    return passes
 
 
 def bench_drt2d(drt3d, synth, dev) -> dict:
@@ -563,18 +585,7 @@ def bench_drt2d(drt3d, synth, dev) -> dict:
     for _ in range(3):
         run()
     t = sorted(_event_ms(run, 7))[3]
-    plan.set_profiling(True)
-    run()
-    torch.cuda.synchronize()
-    passes = {}
-    for name, ms, by in plan.profiled_launches():
-        e = passes.setdefault(name, {"launches": 0, "ms": 0.0, "algo_bytes": 0.0})
-        e["launches"] += 1
-        e["ms"] += ms
-        e["algo_bytes"] += by
-    plan.set_profiling(False)
-    for e in passes.values():
-        e["gbs"] = e["algo_bytes"] / (e["ms"] / 1000) / 1e9
+    passes = profile_launches(plan, run)
     floor = B * N * N * 1.0 + B * 4.0 * N * 2 * N * 4
     del out
     return {"ms": t, "images_per_s": B / (t / 1000), "floor_gbs": floor / (t / 1000) / 1e9, "passes": passes,

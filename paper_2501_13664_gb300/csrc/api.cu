@@ -219,6 +219,14 @@ static int djt_groups(int N, int* G) {
     return 2;
 }
 static int djt_base(int N, int m) { return (N + 1 - (1 << m)) & ~3; }
+// Lines forward: the volume rearranged into the frames of the y- and
+// z-driven sectors (x' = y, y' = z, z' = x and x' = z, y' = x, z' = y), so
+// that every sector's ingest reads runs of z' contiguously.  One copy each.
+static size_t djt_frame_copy_bytes(int N, drt3d_dtype dt) {
+    const size_t esz = dt == DRT3D_U8 ? 1 : dt == DRT3D_I16 ? 2 : 4;
+    return align_up((size_t)N * N * N * esz, 256);
+}
+
 static size_t djt_buf_bytes(int N) {
     int G[2];
     if (djt_groups(N, G) < 2) return 0;
@@ -483,6 +491,7 @@ drt3d_status drt3d_workspace_bytes(const drt3d_plan* P, int op, size_t* bytes) {
         return DRT3D_OK;
     case DRT3D_OP_LINES_FORWARD:
         *bytes = (size_t)kMaxSlots * djt_buf_bytes(P->N);
+        if (*bytes) *bytes += 2 * djt_frame_copy_bytes(P->N, P->dtype);
         return DRT3D_OK;
     case DRT3D_OP_LINES_ADJOINT:
         *bytes = (size_t)kMaxSlots * djt_adj_slot_bytes(P->N);
@@ -730,6 +739,23 @@ drt3d_status djt3d_lines_forward(const drt3d_plan* P, const void* d_in, int32_t*
     const int nslots = popcount12(mask);
     if (npass > 1 && (!d_ws || ws_bytes < (size_t)nslots * buf)) return DRT3D_ERR_WORKSPACE;
     const long long out_block = 4LL * N * N * N * N;  // elements per sector
+    // With room in the workspace, y- and z-driven sectors read frame copies
+    // of the volume (z' contiguous) instead of gathering across it.
+    const size_t fcb = djt_frame_copy_bytes(N, P->dtype);
+    const bool need_y = (mask & 0x0F0u) != 0, need_z = (mask & 0xF00u) != 0;
+    const bool copies = npass > 1 && (need_y || need_z) && ws_bytes >= 2 * fcb + (size_t)nslots * buf;
+    char* ws = static_cast<char*>(d_ws);
+    char* slots = ws + (copies ? 2 * fcb : 0);
+    if (copies) {
+        const int esz = P->dtype == DRT3D_U8 ? 1 : P->dtype == DRT3D_I16 ? 2 : 4;
+        const long long NN = (long long)N * N;
+        prof_begin(P, stream, "djt_frame_copies", (double)(need_y + need_z) * 2 * NN * N * esz);
+        // y-driven frame [y][z][x]: the volume as an N x N^2 matrix, transposed
+        if (need_y && launch_transpose2d(d_in, ws, N, (int)NN, esz, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+        // z-driven frame [z][x][y]: the volume as an N^2 x N matrix, transposed
+        if (need_z && launch_transpose2d(d_in, ws + fcb, NN, N, esz, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+        prof_end(P, stream);
+    }
     DjtLaunch L{};
     L.N = N;
     L.n = n;
@@ -741,9 +767,18 @@ drt3d_status djt3d_lines_forward(const drt3d_plan* P, const void* d_in, int32_t*
         for (int k = 0; k < 12; ++k) {
             if (!((mask >> k) & 1)) continue;
             DjtSlot& sl = L.slot[i];
-            sl.map = sector_affine(N, k);
-            char* b = static_cast<char*>(d_ws) + (size_t)i * buf;
-            sl.in = ingest ? d_in : (const void*)b;
+            const int a = k >> 2;
+            const void* src = d_in;
+            if (copies && a > 0) {
+                // the frame copy is g[x'][y'][z'] with strides N^2, N, 1; the
+                // sector's flips reverse y' (bit 0) and z' (bit 1)
+                src = ws + (a == 1 ? 0 : fcb);
+                sl.map = sector_affine(N, k & 3);
+            } else {
+                sl.map = sector_affine(N, k);
+            }
+            char* b = slots + (size_t)i * buf;
+            sl.in = ingest ? src : (const void*)b;
             sl.out = final_ ? (void*)(d_out + (size_t)i * out_block) : (void*)b;
             ++i;
         }
