@@ -177,7 +177,11 @@ drt3d_status drt3d_planes_inverse(const drt3d_plan* plan, const int32_t* d_R, in
  * Section 4.1).
  *   d_in  : N^3 volume of the plan's dtype (U8, I16 or I32).
  *   d_out : popcount(sector_mask) blocks of N*N*2N*2N int32, overwritten.
- * Errors: INVALID_ARG, DTYPE, ALIGN, WORKSPACE, CUDA. */
+ *   d_ws, ws_bytes: N >= 32 needs one intermediate buffer per selected
+ *           sector; drt3d_workspace_bytes(LINES_FORWARD) adds room for two
+ *           transposed copies of the volume that the y- and z-driven sectors
+ *           then read instead of gathering across it (same result, faster).
+ * N <= 256.  Errors: INVALID_ARG, DTYPE, SIZE, ALIGN, WORKSPACE, CUDA. */
 drt3d_status djt3d_lines_forward(const drt3d_plan* plan, const void* d_in, int32_t* d_out,
                                  uint32_t sector_mask, void* d_ws, size_t ws_bytes,
                                  cudaStream_t stream);
