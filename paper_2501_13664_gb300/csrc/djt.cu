@@ -160,8 +160,8 @@ cudaError_t launch_gk(const DjtLaunch& L, int G, int K, int nslots, cudaStream_t
     if (G == g && K == k) return launch_k<TIn, g, k, INGEST, FINAL>(L, nslots, s);
     DJT_CASE(1, 1) DJT_CASE(1, 2) DJT_CASE(1, 4) DJT_CASE(1, 8)
     DJT_CASE(2, 1) DJT_CASE(2, 2) DJT_CASE(2, 4) DJT_CASE(2, 8)
-    DJT_CASE(3, 1) DJT_CASE(3, 2) DJT_CASE(3, 4) DJT_CASE(3, 8)
-    DJT_CASE(4, 1) DJT_CASE(4, 2) DJT_CASE(4, 4)
+    DJT_CASE(3, 1) DJT_CASE(3, 2) DJT_CASE(3, 3) DJT_CASE(3, 4) DJT_CASE(3, 8)
+    DJT_CASE(4, 1) DJT_CASE(4, 2) DJT_CASE(4, 4) DJT_CASE(4, 5)
 #undef DJT_CASE
     return cudaErrorInvalidValue;
 }
@@ -190,14 +190,30 @@ cudaError_t launch_transpose2d(const void* in, void* out, long long R, int C, in
     return cudaGetLastError();
 }
 
-// Lane width K of a DJT pass writing rows of `width` displacements: the
-// smallest of 1, 2, 4, 8 (4 at most for G = 4) whose warp tile covers the
-// width, else the largest allowed.
+// Lane width K of a DJT pass writing rows of `width` displacements: of the
+// compiled widths (1, 2, 4, 5 for G = 4; 1, 2, 3, 4, 8 below), the one with
+// the fewest lane positions over all tiles of a row (each tile after the
+// first repeats 2^G - 1 positions), the fewer tiles (warps) on a tie.
 int djt_lanes_k(int G, int width) {
-    const int kmax = G >= 4 ? 4 : 8;
-    for (int k = 1; k <= kmax; k *= 2)
-        if (32 * k >= width) return k;
-    return kmax;
+    static const int k4[] = {1, 2, 4, 5};
+    static const int k3[] = {1, 2, 3, 4, 8};
+    const int* ks = G >= 4 ? k4 : k3;
+    const int nk = G >= 4 ? 4 : 5;
+    int best = ks[0], best_tiles = 0;
+    long long best_cost = -1;
+    for (int j = 0; j < nk; ++j) {
+        const int K = ks[j];
+        const int V = (32 * K - ((1 << G) - 1)) & ~3;
+        if (V <= 0) continue;
+        const int tiles = 32 * K >= width ? 1 : 1 + (width - 32 * K + V - 1) / V;
+        const long long cost = (long long)tiles * 32 * K;
+        if (best_cost < 0 || cost < best_cost || (cost == best_cost && tiles < best_tiles)) {
+            best_cost = cost;
+            best = K;
+            best_tiles = tiles;
+        }
+    }
+    return best;
 }
 
 cudaError_t launch_djt_pass(const DjtLaunch& L, int G, int K, drt3d_dtype in_dtype, bool ingest, bool final_,
