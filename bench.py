@@ -511,14 +511,38 @@ def bench_batched(drt3d, synth, dev, tuned) -> dict:
         one_by_one()
     tb = sorted(_event_ms(g.replay, 7))[3]
     t1 = sorted(_event_ms(one_by_one, 7))[3]
+    # mode 1: the same batch as per-volume launches over internal streams,
+    # with the single-volume splits, also replayed from a CUDA graph
+    ms = {}
+    for k in (2, 4, 8):
+        bm = drt3d.BatchPlan(sizes, schedules=sched)
+        bm.set_mode(1, k)
+        bm.bind(vols, outs=outs)
+        with torch.cuda.stream(s):
+            bm.run()
+        torch.cuda.current_stream().wait_stream(s)
+        gm = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gm):
+            bm.run()
+        for _ in range(3):
+            gm.replay()
+        ms[k] = sorted(_event_ms(gm.replay, 7))[3]
+        assert bm.device_error() == 0
+        del gm, bm
+    kbest = min(ms, key=ms.get)
     floor = sum(12.0 * N * N * (3 * N - 2) * 4 + N ** 3 for N in sizes)
-    return {"volumes": len(sizes), "batched_ms": tb, "one_by_one_ms": t1,
-            "batched_volumes_per_s": len(sizes) / (tb / 1000), "one_by_one_volumes_per_s": len(sizes) / (t1 / 1000),
-            "speedup": t1 / tb, "floor_gbs_batched": floor / (tb / 1000) / 1e9,
-            "launches_batched": 1, "launches_one_by_one": sum(len(plans[N].schedule()) for N in sizes),
-            "schedules_batched": {str(N): list(v) for N, v in sorted(bsched.items())},
+    best = min(tb, ms[kbest])
+    return {"volumes": len(sizes), "batched_ms": best, "one_by_one_ms": t1,
+            "batched_mode": "persistent" if tb <= ms[kbest] else f"streams{kbest}",
+            "persistent_ms": tb, "multistream_ms": {str(k): v for k, v in ms.items()},
+            "batched_volumes_per_s": len(sizes) / (best / 1000), "one_by_one_volumes_per_s": len(sizes) / (t1 / 1000),
+            "speedup": t1 / best, "floor_gbs_batched": floor / (best / 1000) / 1e9,
+            "launches_persistent": 1, "launches_one_by_one": sum(len(plans[N].schedule()) for N in sizes),
+            "schedules_persistent": {str(N): list(v) for N, v in sorted(bsched.items())},
             "schedules_one_by_one": {str(N): list(v) for N, v in sorted(sched.items())},
-            "note": "batched = one memset + one persistent kernel, replayed from a CUDA graph; median of 7"}
+            "note": "persistent = one memset + one persistent kernel; multistream = the volumes' per-pass launches "
+                    "over k internal streams; both replayed from a CUDA graph; one-by-one = 96 calls on one "
+                    "stream; medians of 7"}
 
 
 def bench_lines(drt3d, synth, dev) -> dict:

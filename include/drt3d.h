@@ -299,6 +299,16 @@ drt3d_status drt3d_batch_plan_destroy(drt3d_batch_plan* plan);
 drt3d_status drt3d_batch_set_schedule(drt3d_batch_plan* plan, int N, int ngroups, const int* G);
 drt3d_status drt3d_batch_workspace_bytes(const drt3d_batch_plan* plan, size_t* bytes);
 drt3d_status drt3d_batch_bind(drt3d_batch_plan* plan, const drt3d_vol_desc* descs, void* d_ws, size_t ws_bytes);
+/* How drt3d_planes_forward_batched runs the bound batch.
+ *   mode 0 (default): one memset and one persistent kernel for every pass of
+ *           every volume (work items claimed from a counter, dependencies
+ *           through completion counters with bounded waits).
+ *   mode 1: each volume's passes as ordinary kernel launches, the volumes
+ *           spread over `nstreams` (1..8) internal streams, largest first onto
+ *           the least loaded; the streams are forked from and joined back into
+ *           the caller's stream, so the call stays capturable in a CUDA graph.
+ * Results are identical in both modes.  Errors: INVALID_ARG, CUDA. */
+drt3d_status drt3d_batch_set_mode(drt3d_batch_plan* plan, int mode, int nstreams);
 drt3d_status drt3d_planes_forward_batched(const drt3d_batch_plan* plan, cudaStream_t stream);
 drt3d_status drt3d_batch_get_device_error(const drt3d_batch_plan* plan, cudaStream_t stream);
 /* Test and tuning hook: bounded-wait limit in nanoseconds; (withhold_vol,

@@ -124,7 +124,8 @@ class BatchPlan:
     """Planes forward of many uint8 volumes (N in 16..256) in one persistent launch.
 
     ``bind`` fixes the device buffers; ``run`` enqueues one memset and one
-    kernel on the current stream (capturable in a CUDA graph).
+    kernel on the current stream (capturable in a CUDA graph), or with
+    ``set_mode(1)`` the volumes' per-pass launches over internal streams.
     """
 
     def __init__(self, Ns, dtype: torch.dtype = torch.uint8, schedules: dict | None = None):
@@ -165,6 +166,11 @@ class BatchPlan:
         _abi.check(self._lib.drt3d_batch_bind(self.handle, descs, ws.data_ptr(), ws.numel()), "drt3d_batch_bind")
         self._keep = (list(vols), list(outs), ws)
         return outs
+
+    def set_mode(self, mode: int, streams: int = 4) -> None:
+        """0: one persistent kernel (default); 1: per-volume launches spread
+        over ``streams`` internal streams (see drt3d_batch_set_mode)."""
+        _abi.check(self._lib.drt3d_batch_set_mode(self.handle, int(mode), int(streams)), "drt3d_batch_set_mode")
 
     def run(self) -> None:
         _abi.check(self._lib.drt3d_planes_forward_batched(self.handle, _stream()), "drt3d_planes_forward_batched")

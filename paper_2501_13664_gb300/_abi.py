@@ -53,6 +53,7 @@ SIGNATURES = {
     "drt3d_batch_workspace_bytes": (I, [P, ctypes.POINTER(SZ)]),
     "drt3d_batch_bind": (I, [P, P, P, SZ]),
     "drt3d_planes_forward_batched": (I, [P, P]),
+    "drt3d_batch_set_mode": (I, [P, I, I]),
     "drt3d_batch_get_device_error": (I, [P, P]),
     "drt3d_batch_set_wait_limit": (I, [P, ctypes.c_ulonglong, I, I]),
     "drt3d_noalloc_scratch_bytes": (SZ, []),

@@ -26,6 +26,7 @@
 namespace drt3d {
 
 constexpr int kBatchMaxPass = 4;
+constexpr int kBatchMaxStreams = 8;
 
 struct BatchVol {
     CUtensorMap tmap[kBatchMaxPass];  // TMA view of each pass's 16-bit input (passes that stage it)
@@ -252,9 +253,45 @@ struct drt3d_batch_plan {
     int grid = 0;
     unsigned long long wait_ns = 2000000000ull;
     int withhold_vol = -1, withhold_slot = -1;
+    // Mode 1: each volume's passes as ordinary launches, volumes spread over
+    // internal streams (forked from and joined back into the caller's).
+    int mode = 0;
+    int nstreams = 0;
+    cudaStream_t streams[kBatchMaxStreams] = {};
+    cudaEvent_t fork = nullptr, join[kBatchMaxStreams] = {};
+    std::vector<BatchVol> hvols;       // host copy of the bound descriptors
+    std::vector<int> vol_stream;       // stream of each volume
+    std::vector<size_t> vol_slot_stride;
 };
 
 namespace {
+
+void free_streams(drt3d_batch_plan* B) {
+    for (int i = 0; i < B->nstreams; ++i) {
+        if (B->streams[i]) cudaStreamDestroy(B->streams[i]);
+        if (B->join[i]) cudaEventDestroy(B->join[i]);
+        B->streams[i] = nullptr;
+        B->join[i] = nullptr;
+    }
+    if (B->fork) cudaEventDestroy(B->fork);
+    B->fork = nullptr;
+    B->nstreams = 0;
+}
+
+// Volumes to streams, largest first onto the least loaded stream (work ~ N^3).
+void assign_streams(drt3d_batch_plan* B) {
+    const int k = std::max(1, B->nstreams);
+    std::vector<int> order(B->count);
+    for (int v = 0; v < B->count; ++v) order[v] = v;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return B->Ns[a] > B->Ns[b]; });
+    std::vector<double> load(k, 0.0);
+    B->vol_stream.assign(B->count, 0);
+    for (int v : order) {
+        const int s = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        B->vol_stream[v] = s;
+        load[s] += (double)B->Ns[v] * B->Ns[v] * B->Ns[v];
+    }
+}
 
 void free_bound(drt3d_batch_plan* B) {
     cudaFree(B->d_vols);
@@ -300,6 +337,7 @@ drt3d_status drt3d_batch_plan_create(drt3d_batch_plan** plan, int count, const i
 drt3d_status drt3d_batch_plan_destroy(drt3d_batch_plan* B) {
     if (!B) return DRT3D_OK;
     free_bound(B);
+    free_streams(B);
     cudaFree(B->d_status);
     delete B;
     return DRT3D_OK;
@@ -341,6 +379,7 @@ drt3d_status drt3d_batch_bind(drt3d_batch_plan* B, const drt3d_vol_desc* descs, 
     }
     if (((uintptr_t)d_ws & 15)) return DRT3D_ERR_ALIGN;
     free_bound(B);
+    B->vol_slot_stride.clear();
     std::vector<BatchVol> vols(B->count);
     char* ws = static_cast<char*>(d_ws);
     int maxpass = 0;
@@ -385,8 +424,11 @@ drt3d_status drt3d_batch_bind(drt3d_batch_plan* B, const drt3d_vol_desc* descs, 
             bv.out_kind[p] = (int)ps.out_kind;
             bv.ctas[p] = (unsigned)(L.ctas / L.ntiles);
         }
+        B->vol_slot_stride.push_back(2 * buf);
         ws += align_up(vol_ws_bytes(S), 256);
     }
+    B->hvols = vols;
+    assign_streams(B);
     // pass-major segments
     std::vector<unsigned> seg_start;
     std::vector<int> seg_vol, seg_pass;
@@ -421,8 +463,63 @@ drt3d_status drt3d_batch_bind(drt3d_batch_plan* B, const drt3d_vol_desc* descs, 
     return DRT3D_OK;
 }
 
+drt3d_status drt3d_batch_set_mode(drt3d_batch_plan* B, int mode, int nstreams) {
+    if (!B || (mode != 0 && mode != 1)) return DRT3D_ERR_INVALID_ARG;
+    if (mode == 1 && (nstreams < 1 || nstreams > kBatchMaxStreams)) return DRT3D_ERR_INVALID_ARG;
+    free_streams(B);
+    B->mode = mode;
+    if (mode == 1) {
+        for (int i = 0; i < nstreams; ++i) {
+            if (cudaStreamCreateWithFlags(&B->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&B->join[i], cudaEventDisableTiming) != cudaSuccess) {
+                B->nstreams = i + 1;
+                free_streams(B);
+                B->mode = 0;
+                return DRT3D_ERR_CUDA;
+            }
+        }
+        B->nstreams = nstreams;
+        if (cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess) {
+            free_streams(B);
+            B->mode = 0;
+            return DRT3D_ERR_CUDA;
+        }
+    }
+    if (B->bound) assign_streams(B);
+    return DRT3D_OK;
+}
+
 drt3d_status drt3d_planes_forward_batched(const drt3d_batch_plan* B, cudaStream_t stream) {
     if (!B || !B->bound) return DRT3D_ERR_INVALID_ARG;
+    if (B->mode == 1) {
+        // pass-major over the volumes; a volume's passes stay on its stream
+        if (cudaEventRecord(B->fork, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+        for (int i = 0; i < B->nstreams; ++i)
+            if (cudaStreamWaitEvent(B->streams[i], B->fork, 0) != cudaSuccess) return DRT3D_ERR_CUDA;
+        int maxpass = 0;
+        for (const BatchVol& bv : B->hvols) maxpass = std::max(maxpass, bv.npass);
+        for (int p = 0; p < maxpass; ++p)
+            for (int v = 0; v < B->count; ++v) {
+                const BatchVol& bv = B->hvols[v];
+                if (p >= bv.npass) continue;
+                FusedLaunch L = bv.pass[p];
+                L.status = B->d_status;
+                const cudaStream_t st = B->streams[B->vol_stream[v]];
+                cudaError_t e;
+                if (bv.tma[p])
+                    e = launch_planes_fused_tma(L, bv.G[p], (ElemKind)bv.out_kind[p], L.slot[0].in,
+                                                B->vol_slot_stride[v], 12, st);
+                else
+                    e = launch_planes_fused(L, bv.G[p], (ElemKind)bv.in_kind[p], (ElemKind)bv.out_kind[p], p == 0,
+                                            12, st);
+                if (e != cudaSuccess) return DRT3D_ERR_CUDA;
+            }
+        for (int i = 0; i < B->nstreams; ++i) {
+            if (cudaEventRecord(B->join[i], B->streams[i]) != cudaSuccess) return DRT3D_ERR_CUDA;
+            if (cudaStreamWaitEvent(stream, B->join[i], 0) != cudaSuccess) return DRT3D_ERR_CUDA;
+        }
+        return DRT3D_OK;
+    }
     if (cudaMemsetAsync(B->d_counters, 0, B->counters_bytes, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
     BatchArgs A;
     A.vols = B->d_vols;
