@@ -46,10 +46,12 @@ namespace {
 
 __host__ __device__ constexpr int inv_warps(int G) { return G >= 4 ? 8 : (1 << (G - 1)); }
 
-// Chunk width: 8 up to 256 displacements (one segment), 16 up to 1024 (one
-// or two segments: smaller register and shared-memory footprint, so three
-// CTAs fit an SM, beats one segment of 24-wide chunks), 32 beyond.
-__host__ __device__ inline int inv_chunk_width(int W) { return W <= 256 ? 8 : W <= 1024 ? 16 : 32; }
+// Chunk width: 8 up to 384 displacements (one or two segments; four CTAs
+// fit an SM), 16 up to 1024 (one or two segments: three CTAs per SM, which
+// beats one segment of 24-wide chunks at two), 32 beyond.  The second
+// segment of a short row keeps only a few lanes busy, but the shorter chains
+// and higher occupancy more than pay for it.
+__host__ __device__ inline int inv_chunk_width(int W) { return W <= 384 ? 8 : W <= 1024 ? 16 : 32; }
 
 // Prefix chunks of a slot: the shifted copy of a half-stage with slope so
 // far S reads down to displacement -(S + 3); S < 2^(m0 + G - 1).
@@ -194,7 +196,7 @@ __device__ __forceinline__ void stage_pair(uint32_t* s0, uint32_t* s1, int off0,
 // MULTI: rows of more than 32 chunks, scanned in segments of 32 chunks from
 // the top with a carry; otherwise one segment.
 template <int G, int CH, bool MULTI>
-__global__ void __launch_bounds__(inv_warps(G) * 32, (G >= 4 ? (CH <= 16 ? 3 : 2) : 4))
+__global__ void __launch_bounds__(inv_warps(G) * 32, (G >= 4 ? (CH <= 8 ? 4 : CH <= 16 ? 3 : 2) : 4))
 planes_inv_pass(const __grid_constant__ InvLaunch L) {
     constexpr int R = 1 << G;
     constexpr int NW = inv_warps(G);
@@ -455,7 +457,8 @@ template <int G>
 cudaError_t launch_inv_g(const InvLaunch& L, cudaStream_t s) {
     const int W = L.dmax - L.gin.base;
     switch (inv_chunk_width(W)) {
-    case 8: return launch_inv_gc<G, 8, false>(L, s);
+    case 8:
+        return (W + 7) / 8 > 32 ? launch_inv_gc<G, 8, true>(L, s) : launch_inv_gc<G, 8, false>(L, s);
     case 16:
         return (W + 15) / 16 > 32 ? launch_inv_gc<G, 16, true>(L, s) : launch_inv_gc<G, 16, false>(L, s);
     default:
