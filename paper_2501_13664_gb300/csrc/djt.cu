@@ -122,31 +122,6 @@ djt_pass(const __grid_constant__ DjtLaunch L) {
     }
 }
 
-// out = in^T for an R x C row-major matrix, through 32 x 32 tiles in shared
-// memory (both the reads and the writes coalesced).
-template <typename T>
-__global__ void __launch_bounds__(256) transpose2d(const T* __restrict__ in, T* __restrict__ out, long long R, int C,
-                                                   long long tilesC) {
-    __shared__ T tile[32][33];
-    const long long b = blockIdx.x;
-    const long long r0 = (b / tilesC) * 32;
-    const int c0 = (int)(b % tilesC) * 32;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = ty; k < 32; k += 8) {
-        const long long r = r0 + k;
-        const int c = c0 + tx;
-        if (r < R && c < C) tile[k][tx] = in[r * C + c];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = ty; k < 32; k += 8) {
-        const int c = c0 + k;
-        const long long r = r0 + tx;
-        if (r < R && c < C) out[(long long)c * R + r] = tile[tx][k];
-    }
-}
-
 template <typename TIn, int G, int K, bool INGEST, bool FINAL>
 cudaError_t launch_k(const DjtLaunch& L, int nslots, cudaStream_t s) {
     const long long blocks = (L.warps + kDjtWarps - 1) / kDjtWarps;
@@ -167,28 +142,6 @@ cudaError_t launch_gk(const DjtLaunch& L, int G, int K, int nslots, cudaStream_t
 }
 
 }  // namespace
-
-cudaError_t launch_transpose2d(const void* in, void* out, long long R, int C, int esz, cudaStream_t s) {
-    const long long tilesC = (C + 31) / 32;
-    const long long blocks = ((R + 31) / 32) * tilesC;
-    switch (esz) {
-    case 1:
-        transpose2d<uint8_t><<<(unsigned)blocks, 256, 0, s>>>(static_cast<const uint8_t*>(in),
-                                                              static_cast<uint8_t*>(out), R, C, tilesC);
-        break;
-    case 2:
-        transpose2d<uint16_t><<<(unsigned)blocks, 256, 0, s>>>(static_cast<const uint16_t*>(in),
-                                                               static_cast<uint16_t*>(out), R, C, tilesC);
-        break;
-    case 4:
-        transpose2d<uint32_t><<<(unsigned)blocks, 256, 0, s>>>(static_cast<const uint32_t*>(in),
-                                                               static_cast<uint32_t*>(out), R, C, tilesC);
-        break;
-    default:
-        return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
 
 // Lane width K of a DJT pass writing rows of `width` displacements: of the
 // compiled widths (1, 2, 4, 5 for G = 4; 1, 2, 3, 4, 8 below), the one with

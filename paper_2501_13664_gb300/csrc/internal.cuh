@@ -200,7 +200,7 @@ struct DjtLaunch {
     long long warps;         // warps per slot
 };
 int djt_lanes_k(int G, int width);
-// out = in^T for an R x C row-major matrix of esz-byte elements (djt.cu).
+// out = in^T for an R x C row-major matrix of esz-byte elements (transpose.cu).
 cudaError_t launch_transpose2d(const void* in, void* out, long long R, int C, int esz, cudaStream_t s);
 
 // One stage of the lines adjoint, stage m + 1 -> m (djt_adjoint.cu).

@@ -32,6 +32,20 @@ def test_lines_integer_exact(drt, oracle_mod, N, dt):
     np.testing.assert_array_equal(_fwd(drt, f), oracle_mod.lines_forward(f))
 
 
+@pytest.mark.parametrize("dt", ["u8", "i32"])
+def test_lines_n64_frame_copies(drt, oracle_mod, dt):
+    """N = 64: the y- and z-driven sectors read transposed copies of the
+    volume (the 64 x 64-tile byte transpose for uint8, the element transpose
+    otherwise); bit-exact against the oracle."""
+    N = 64
+    if dt == "u8":
+        f = synth.random_int32((N, N, N), 90, 0, 256).astype(np.uint8)
+    else:
+        f = synth.random_int32((N, N, N), 91)
+    ks = [5, 10]
+    np.testing.assert_array_equal(_fwd(drt, f, ks), oracle_mod.lines_forward(f, ks))
+
+
 def test_lines_sector_subsets(drt, oracle_mod):
     N = 16
     f = synth.c3_volume(N, seed=7)
