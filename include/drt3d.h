@@ -218,8 +218,10 @@ drt3d_status djt3d_lines_adjoint(const drt3d_plan* plan, const int32_t* d_cot, i
  *   steps : host array of n + 1 floats, steps[l] > 0 for l = 1..n (entry 0
  *           unused); steps[l] = factor / drt3d_press_spectral_radius(l) with
  *           factor < 2 makes each smoothing step contract.
- *   d_ws, ws_bytes: >= drt3d_workspace_bytes(PLANES_PRESS) (about 450 N^3
- *           bytes plus the forward's workspace).
+ *   d_ws, ws_bytes: >= drt3d_workspace_bytes(PLANES_PRESS): about 320 N^3
+ *           bytes (residuals of every level, one transform-sized buffer,
+ *           per-level solutions) plus the larger of the forward's and the
+ *           adjoint's workspace; N = 1024 does not fit a 288 GB device.
  * Plan dtype must be F32.  The coarser levels' plans are created (host
  * memory only) on first use and released with the plan.  Errors:
  * INVALID_ARG, DTYPE, ALIGN, WORKSPACE, NO_MEMORY, CUDA. */

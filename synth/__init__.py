@@ -30,6 +30,8 @@ Workloads (numpy ``default_rng(seed)`` throughout):
                      random centre, semi-axes N/10..N/3 and intensity 0.2..1
                      (seed 7); stands in for the paper's 128^3 head and spine
                      MRI inversions (the scans themselves are not available).
+* ``dense_u8``    -- N^3 uint8 uniform 0..255, drawn directly as bytes (the
+                     maximum-size tests, N up to 1024).
 """
 from __future__ import annotations
 
@@ -198,3 +200,9 @@ def phantom(N: int = 128, seed: int = 7, blobs: int = 6) -> np.ndarray:
         v = rng.uniform(0.2, 1.0)
         f += v * ((((X - c[0]) / a[0]) ** 2 + ((Y - c[1]) / a[1]) ** 2 + ((Z - c[2]) / a[2]) ** 2) <= 1.0)
     return f.astype(np.float32)
+
+
+def dense_u8(N: int, seed: int) -> np.ndarray:
+    """Uniform uint8 volume, generated without a wider intermediate."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, 256, size=(N, N, N), dtype=np.uint8)
