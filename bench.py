@@ -362,20 +362,23 @@ def run_ours(args):
     plan.set_profiling(False)
     if have_inverse:
         iplan.set_profiling(False)
+    # per launch name: total ms, launches, total algorithmic bytes (a pass
+    # split into several launches sums its parts)
     by_name: dict = {}
     for name, t, b in launches:
         e = by_name.setdefault(name, [0.0, 0, 0.0])
         e[0] += t
         e[1] += 1
-        e[2] = b
+        e[2] += b
     dom = max(by_name.items(), key=lambda kv: kv[1][0])
-    dom_name, (dom_tot, dom_cnt, dom_bytes) = dom
+    dom_name, (dom_tot, dom_cnt, dom_bytes_tot) = dom
     dom_ms = dom_tot / dom_cnt
+    dom_bytes = dom_bytes_tot / dom_cnt
     peaks = measured_peaks()
     achieved = dom_bytes / (dom_ms / 1000.0) / 1e9
     floor_bytes = 12.0 * N * N * (3 * N - 2) * 4 + N ** 3  # input once + final output
-    kernels = {nm: {"launches": c, "avg_ms": tot / c, "algo_bytes": b,
-                    "gbs": b / (tot / c / 1000.0) / 1e9} for nm, (tot, c, b) in by_name.items()}
+    kernels = {nm: {"launches": c, "avg_ms": tot / c, "algo_bytes": b / c,
+                    "gbs": b / (tot / 1000.0) / 1e9} for nm, (tot, c, b) in by_name.items()}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
