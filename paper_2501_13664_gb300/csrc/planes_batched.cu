@@ -35,7 +35,9 @@ struct BatchVol {
     int npass;
     int G[kBatchMaxPass];
     int in_kind[kBatchMaxPass], out_kind[kBatchMaxPass];
-    unsigned ctas[kBatchMaxPass];  // items (units, each all its tiles) per dodecant slot
+    unsigned ctas[kBatchMaxPass];  // items per dodecant slot
+    unsigned upi[kBatchMaxPass];   // units per item (each unit with all its tiles)
+    unsigned units[kBatchMaxPass]; // units per dodecant slot
 };
 
 struct BatchArgs {
@@ -85,9 +87,9 @@ __device__ bool wait_counter(const BatchArgs& A, const unsigned* ctr, unsigned t
 // through a global pointer, the compiler would have to reload them after every
 // store (it cannot prove the output buffers do not alias the tables).
 template <typename TIn, typename TOut, typename TS, int G, bool INGEST, bool TMA = false>
-__device__ __forceinline__ void run_g(const FusedLaunch& Lg, int slot, unsigned cta, unsigned char* smem,
-                                      const CUtensorMap* tmap = nullptr, uint64_t* mbar = nullptr,
-                                      int* status = nullptr) {
+__device__ __forceinline__ void run_g(const FusedLaunch& Lg, int slot, unsigned item, unsigned upi, unsigned units,
+                                      unsigned char* smem, const CUtensorMap* tmap = nullptr,
+                                      uint64_t* mbar = nullptr, int* status = nullptr) {
     FusedLaunch L;
     L.N = Lg.N;
     L.n = Lg.n;
@@ -102,25 +104,27 @@ __device__ __forceinline__ void run_g(const FusedLaunch& Lg, int slot, unsigned 
     L.status = status;
     L.global_layout = 0;
     const FusedSlot sp = Lg.slot[slot];
-    // one item = one unit: all its displacement tiles
+    // one item = `upi` consecutive units, each with all its displacement tiles
     const unsigned nt = (unsigned)L.ntiles;
-    for (unsigned t = 0; t < nt; ++t) {
-        if (t > 0) __syncthreads();  // the previous tile's phase 2 is done with shared memory
+    const unsigned c0 = item * upi * nt, c1 = min(item * upi + upi, units) * nt;
+    for (unsigned c = c0; c < c1; ++c) {
+        if (c > c0) __syncthreads();  // the previous tile's phase 2 is done with shared memory
         if constexpr (TMA)
-            fused_cta<TIn, TOut, uint32_t, TS, G, false, true, true>(L, sp, cta * nt + t, smem, tmap, slot, mbar);
+            fused_cta<TIn, TOut, uint32_t, TS, G, false, true, true>(L, sp, c, smem, tmap, slot, mbar);
         else if constexpr (INGEST && G == 4 && std::is_same<TIn, uint8_t>::value && std::is_same<TS, uint16_t>::value)
-            fused_cta_u8x2<TOut, G>(L, sp, cta * nt + t, smem);  // 16-bit sums: two groups per register
+            fused_cta_u8x2<TOut, G>(L, sp, c, smem);  // 16-bit sums: two groups per register
         else
-            fused_cta<TIn, TOut, uint32_t, TS, G, INGEST, true>(L, sp, cta * nt + t, smem);
+            fused_cta<TIn, TOut, uint32_t, TS, G, INGEST, true>(L, sp, c, smem);
     }
 }
 
 template <typename TIn, typename TOut, typename TS, bool INGEST>
-__device__ __forceinline__ void run_kind(const FusedLaunch& L, int G, int slot, unsigned cta, unsigned char* smem) {
+__device__ __forceinline__ void run_kind(const FusedLaunch& L, int G, int slot, unsigned item, unsigned upi,
+                                         unsigned units, unsigned char* smem) {
     switch (G) {
-    case 2: run_g<TIn, TOut, TS, 2, INGEST>(L, slot, cta, smem); break;
-    case 3: run_g<TIn, TOut, TS, 3, INGEST>(L, slot, cta, smem); break;
-    default: run_g<TIn, TOut, TS, 4, INGEST>(L, slot, cta, smem); break;
+    case 2: run_g<TIn, TOut, TS, 2, INGEST>(L, slot, item, upi, units, smem); break;
+    case 3: run_g<TIn, TOut, TS, 3, INGEST>(L, slot, item, upi, units, smem); break;
+    default: run_g<TIn, TOut, TS, 4, INGEST>(L, slot, item, upi, units, smem); break;
     }
 }
 
@@ -166,28 +170,33 @@ __global__ void __launch_bounds__(256, 2) planes_batched(const __grid_constant__
         const FusedLaunch& L = B.pass[p];
         const int G = B.G[p];
         const int ik = B.in_kind[p], ok = B.out_kind[p];
+        const unsigned upi = B.upi[p], units = B.units[p];
         if (p == 0) {
-            if (ok == (int)ElemKind::U16) run_kind<uint8_t, uint16_t, uint16_t, true>(L, G, slot, cta, smem);
-            else run_kind<uint8_t, uint32_t, uint16_t, true>(L, G, slot, cta, smem);
+            if (ok == (int)ElemKind::U16) run_kind<uint8_t, uint16_t, uint16_t, true>(L, G, slot, cta, upi, units, smem);
+            else run_kind<uint8_t, uint32_t, uint16_t, true>(L, G, slot, cta, upi, units, smem);
         } else if (B.tma[p]) {
             // 16-bit input staged by TMA (G >= 3)
             const CUtensorMap* tm = &B.tmap[p];
             if (G == 4) {
                 if (ok == (int)ElemKind::U16)
-                    run_g<uint16_t, uint16_t, uint32_t, 4, false, true>(L, slot, cta, smem, tm, mbar, A.status);
+                    run_g<uint16_t, uint16_t, uint32_t, 4, false, true>(L, slot, cta, upi, units, smem, tm, mbar,
+                                                                        A.status);
                 else
-                    run_g<uint16_t, uint32_t, uint32_t, 4, false, true>(L, slot, cta, smem, tm, mbar, A.status);
+                    run_g<uint16_t, uint32_t, uint32_t, 4, false, true>(L, slot, cta, upi, units, smem, tm, mbar,
+                                                                        A.status);
             } else {
                 if (ok == (int)ElemKind::U16)
-                    run_g<uint16_t, uint16_t, uint32_t, 3, false, true>(L, slot, cta, smem, tm, mbar, A.status);
+                    run_g<uint16_t, uint16_t, uint32_t, 3, false, true>(L, slot, cta, upi, units, smem, tm, mbar,
+                                                                        A.status);
                 else
-                    run_g<uint16_t, uint32_t, uint32_t, 3, false, true>(L, slot, cta, smem, tm, mbar, A.status);
+                    run_g<uint16_t, uint32_t, uint32_t, 3, false, true>(L, slot, cta, upi, units, smem, tm, mbar,
+                                                                        A.status);
             }
         } else if (ik == (int)ElemKind::U16) {
-            if (ok == (int)ElemKind::U16) run_kind<uint16_t, uint16_t, uint32_t, false>(L, G, slot, cta, smem);
-            else run_kind<uint16_t, uint32_t, uint32_t, false>(L, G, slot, cta, smem);
+            if (ok == (int)ElemKind::U16) run_kind<uint16_t, uint16_t, uint32_t, false>(L, G, slot, cta, upi, units, smem);
+            else run_kind<uint16_t, uint32_t, uint32_t, false>(L, G, slot, cta, upi, units, smem);
         } else {
-            run_kind<uint32_t, uint32_t, uint32_t, false>(L, G, slot, cta, smem);
+            run_kind<uint32_t, uint32_t, uint32_t, false>(L, G, slot, cta, upi, units, smem);
         }
         // Signal completion only where a later pass depends on it.
         if (p + 1 < B.npass) {
@@ -422,7 +431,12 @@ drt3d_status drt3d_batch_bind(drt3d_batch_plan* B, const drt3d_vol_desc* descs, 
                 return DRT3D_ERR_CUDA;
             bv.in_kind[p] = (int)ps.in_kind;
             bv.out_kind[p] = (int)ps.out_kind;
-            bv.ctas[p] = (unsigned)(L.ctas / L.ntiles);
+            // Small units (2^G x 2^G rows) are grouped so that an item carries
+            // at least 256 rows: its claim, dependency wait and barriers would
+            // otherwise cost more than its work.
+            bv.units[p] = (unsigned)(L.ctas / L.ntiles);
+            bv.upi[p] = ps.G >= 4 ? 1u : (ps.G == 3 ? 4u : (ps.G == 2 ? 16u : 64u));
+            bv.ctas[p] = (bv.units[p] + bv.upi[p] - 1) / bv.upi[p];
         }
         B->vol_slot_stride.push_back(2 * buf);
         ws += align_up(vol_ws_bytes(S), 256);
