@@ -107,10 +107,14 @@ __device__ __forceinline__ void run_g(const FusedLaunch& Lg, int slot, unsigned 
     // one item = `upi` consecutive units, each with all its displacement tiles
     const unsigned nt = (unsigned)L.ntiles;
     const unsigned c0 = item * upi * nt, c1 = min(item * upi + upi, units) * nt;
+    // The staged rows were written by other CTAs through the generic proxy
+    // (made visible to this one by the dependency wait): one proxy fence per
+    // thread orders them before all of this item's TMA reads.
+    if constexpr (TMA) tma::fence_proxy_async_global();
     for (unsigned c = c0; c < c1; ++c) {
         if (c > c0) __syncthreads();  // the previous tile's phase 2 is done with shared memory
         if constexpr (TMA)
-            fused_cta<TIn, TOut, uint32_t, TS, G, false, true, true>(L, sp, c, smem, tmap, slot, mbar);
+            fused_cta<TIn, TOut, uint32_t, TS, G, false, false, true>(L, sp, c, smem, tmap, slot, mbar);
         else if constexpr (INGEST && G == 4 && std::is_same<TIn, uint8_t>::value && std::is_same<TS, uint16_t>::value)
             fused_cta_u8x2<TOut, G>(L, sp, c, smem);  // 16-bit sums: two groups per register
         else
