@@ -640,7 +640,7 @@ def bench_drt2d(drt3d, synth, dev) -> dict:
     del out
     return {"ms": t, "images_per_s": B / (t / 1000), "floor_gbs": floor / (t / 1000) / 1e9, "passes": passes,
             "workload": "512 uint8 images 256x256 (5 % pixels 1..255 + 4 lines of 255 each), four quadrants, "
-                        "int32 out; chunks of images sized so intermediates stay in L2"}
+                        "int32 out; one CTA per (image, quadrant), 16-bit intermediate rows in shared memory"}
 
 
 def bench_press(drt3d, synth, dev) -> dict:

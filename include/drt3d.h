@@ -253,7 +253,10 @@ drt3d_status drt3d_press_spectral_radius(const drt3d_plan* plan, int level, cons
  *   d_ws, ws_bytes: workspace for the intermediate stages of one chunk of
  *           images; drt2d_workspace_bytes() gives a size that keeps a chunk's
  *           intermediates near 32 MiB.  Any size that holds one image works
- *           (images are processed in chunks of what fits); N <= 16 needs none.
+ *           (images are processed in chunks of what fits).  None is needed
+ *           for N <= 16, nor for uint8 images with N <= 256 (each image and
+ *           quadrant is transformed by one CTA with its intermediate rows in
+ *           shared memory as 16-bit values, exact since N * 255 < 2^16).
  *   B = 0 is a no-op.  Integer input is exact in wrapping int32; float input
  *   is summed in float32 in a fixed order.  Errors: INVALID_ARG, ALIGN,
  *   WORKSPACE, CUDA. */

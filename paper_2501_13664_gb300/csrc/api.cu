@@ -985,7 +985,7 @@ drt3d_status drt2d_workspace_bytes(const drt3d_plan* P, int B, uint32_t qmask, s
     int nbuf;
     const size_t slot = drt2d_slot_bytes(P->N, &nbuf);
     const int nq = quad_count(qmask);
-    if (nbuf == 0 || B == 0) {
+    if (nbuf == 0 || B == 0 || drt2d_fused_supported(P->N, P->dtype)) {
         *bytes = 0;
         return DRT3D_OK;
     }
@@ -1004,6 +1004,23 @@ drt3d_status drt2d_forward(const drt3d_plan* P, const void* d_img, int B, void* 
     if (!aligned16(d_img) || !aligned16(d_out) || !aligned16(d_ws)) return DRT3D_ERR_ALIGN;
     const int N = P->N, n = P->n;
     const int nq = quad_count(qmask);
+    if (drt2d_fused_supported(N, P->dtype)) {
+        // one CTA per (image, quadrant), intermediates in shared memory
+        Drt2dLaunch F{};
+        F.in = d_img;
+        F.out = d_out;
+        F.N = N;
+        F.n = n;
+        F.nq = nq;
+        for (int q = 0, i = 0; q < 4; ++q)
+            if ((qmask >> q) & 1) F.quad[i++] = q;
+        const long long nslots = (long long)B * nq;
+        if (nslots > 0x7fffffffLL) return DRT3D_ERR_INVALID_ARG;
+        prof_begin(P, stream, "drt2d_fused", (double)B * N * N + (double)nslots * N * 2 * N * 4);
+        if (launch_drt2d_fused(F, (int)nslots, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+        prof_end(P, stream);
+        return DRT3D_OK;
+    }
     int nbuf;
     const size_t slot_bytes = drt2d_slot_bytes(N, &nbuf);
     const long long chunk = drt2d_chunk(N, nq, B, ws_bytes);

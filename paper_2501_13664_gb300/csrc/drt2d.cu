@@ -178,7 +178,144 @@ cudaError_t launch_g(const Drt2dLaunch& L, int G, int nslots, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Whole transform of one (image, quadrant) per CTA, for uint8 images with
+// N = 2^(G1 + G2) <= 256 and a two-group schedule.  Every partial sum is at
+// most N * 255 <= 65280, so the first group's output rows -- N rows over
+// [base1, 2N) -- stay in shared memory as 16-bit values; the second group
+// reads them back and writes the final rows.  Warp work items are (unit,
+// tile) pairs of each group, exactly as in drt2d_pass.
+template <int G1, int G2, int NW>
+__global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : 2) drt2d_fused(const __grid_constant__ Drt2dLaunch L) {
+    constexpr int K = kK2;
+    constexpr int R1 = 1 << G1, R2 = 1 << G2;
+    constexpr int N = R1 * R2, W = 2 * N;
+    constexpr int base1 = (N + 1 - R1) & ~3;  // nothing below is non-zero after G1 stages
+    constexpr int W1 = W - base1;
+    constexpr int P1 = (W1 + 7) & ~7;         // 16-byte rows
+    constexpr int V1 = (32 * K - (R1 - 1)) & ~3, T1 = (W1 + V1 - 1) / V1;
+    constexpr int V2 = (32 * K - (R2 - 1)) & ~3, T2 = (W + V2 - 1) / V2;
+    extern __shared__ __align__(16) uint16_t rows1[];  // [N][P1], element d at d - base1
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slot = blockIdx.x;
+    const int q = L.quad[slot % L.nq];
+    const uint8_t* img = static_cast<const uint8_t*>(L.in) + (long long)(slot / L.nq) * N * N;
+
+    // ---- group 1: G1 stages from the image (sg = 0: rows a0 + u, unsheared)
+#pragma unroll 1
+    for (int it = warp; it < (N / R1) * T1; it += NW) {
+        const int wq = it / T1, tile = it - wq * T1;
+        const int pos0 = base1 + tile * V1 + lane * K;
+        const int a0 = wq * R1;
+        const int y0 = pos0 - N;  // a multiple of K, as N is: all K pixels in or all out
+        uint32_t v[R1][K];
+        if (q & 2) {
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const int y = y0 + i;
+                uint8_t run[R1];
+                if ((unsigned)y < (unsigned)N) {
+                    load_run<uint8_t, R1>(img + ((q & 1) ? N - 1 - y : y) * N + a0, run);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < R1; ++u) run[u] = 0;
+                }
+#pragma unroll
+                for (int u = 0; u < R1; ++u) v[u][i] = run[u];
+            }
+        } else {
+            const bool in = (unsigned)y0 < (unsigned)N;
+#pragma unroll
+            for (int u = 0; u < R1; ++u) {
+                uint8_t run[K];
+                if (in) {
+                    load_run<uint8_t, K>(img + (a0 + u) * N + ((q & 1) ? N - K - y0 : y0), run);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < K; ++i) run[i] = 0;
+                }
+                if (q & 1) {
+#pragma unroll
+                    for (int i = 0; i < K; ++i) v[u][i] = run[K - 1 - i];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < K; ++i) v[u][i] = run[i];
+                }
+            }
+        }
+        fwd_all<G1, K>(v);
+        if (lane * K < V1 && pos0 < W) {
+#pragma unroll
+            for (int t = 0; t < R1; ++t) {
+                const uint2 w = make_uint2(v[t][0] | (v[t][1] << 16), v[t][2] | (v[t][3] << 16));
+                *reinterpret_cast<uint2*>(rows1 + (a0 + t) * P1 + (pos0 - base1)) = w;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- group 2: G2 stages, slopes so far sg < R1, rows sg + u R1 sheared by sg u
+    uint32_t* out = static_cast<uint32_t*>(L.out) + (long long)slot * N * W;
+#pragma unroll 1
+    for (int it = warp; it < R1 * T2; it += NW) {
+        const int sg = it / T2, tile = it - sg * T2;
+        const int pos0 = tile * V2 + lane * K;
+        uint32_t v[R2][K];
+#pragma unroll
+        for (int u = 0; u < R2; ++u) {
+            const uint16_t* row = rows1 + (sg + u * R1) * P1 - base1;
+            const int ds = pos0 + sg * u;
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const int d = ds + i;
+                v[u][i] = (d >= base1 && d < W) ? (uint32_t)row[d] : 0u;
+            }
+        }
+        fwd_all<G2, K>(v);
+        if (lane * K < V2 && pos0 < W) {
+#pragma unroll
+            for (int t = 0; t < R2; ++t)
+                *reinterpret_cast<uint4*>(out + (long long)(t + (sg << G2)) * W + pos0) =
+                    make_uint4(v[t][0], v[t][1], v[t][2], v[t][3]);
+        }
+    }
+}
+
+template <int G1, int G2, int NW>
+cudaError_t launch_fused2(const Drt2dLaunch& L, int nslots, cudaStream_t s) {
+    constexpr int N = 1 << (G1 + G2);
+    constexpr int base1 = (N + 1 - (1 << G1)) & ~3;
+    constexpr int P1 = (2 * N - base1 + 7) & ~7;
+    constexpr size_t smem = (size_t)N * P1 * 2;
+    auto kern = drt2d_fused<G1, G2, NW>;
+    if (smem > 48 * 1024) {
+        static unsigned long long attr_done = 0;  // one bit per device
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev >= 64 || !((attr_done >> dev) & 1ull)) {
+            const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            if (dev < 64) attr_done |= 1ull << dev;
+        }
+    }
+    kern<<<(unsigned)nslots, NW * 32, smem, s>>>(L);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+bool drt2d_fused_supported(int N, drt3d_dtype dtype) {
+    return dtype == DRT3D_U8 && N >= 32 && N <= 256;
+}
+
+cudaError_t launch_drt2d_fused(const Drt2dLaunch& L, int nslots, cudaStream_t s) {
+    switch (L.N) {
+    case 32: return launch_fused2<3, 2, 8>(L, nslots, s);
+    case 64: return launch_fused2<3, 3, 8>(L, nslots, s);
+    case 128: return launch_fused2<4, 3, 8>(L, nslots, s);
+    case 256: return launch_fused2<4, 4, 16>(L, nslots, s);
+    }
+    return cudaErrorInvalidValue;
+}
 
 int drt2d_tile_valid(int G) { return (32 * kK2 - ((1 << G) - 1)) & ~3; }
 

@@ -247,6 +247,11 @@ struct Drt2dLaunch {
     int vec_ingest;          // first pass: image rows allow 16-byte vector loads
 };
 int drt2d_tile_valid(int G);
+// The whole transform of each (image, quadrant) in one CTA (uint8 images,
+// 32 <= N <= 256: first-group rows kept as 16 bits in shared memory).  Slot i
+// of L reads image i / nq and writes its (N, 2N) block at out + i N 2N.
+bool drt2d_fused_supported(int N, drt3d_dtype dtype);
+cudaError_t launch_drt2d_fused(const Drt2dLaunch& L, int nslots, cudaStream_t s);
 cudaError_t launch_drt2d_pass(const Drt2dLaunch& L, int G, drt3d_dtype in_dtype, bool ingest, int nslots,
                               cudaStream_t s);
 

@@ -41,6 +41,18 @@ def test_integer_exact(drt, oracle_mod, N, dt):
     np.testing.assert_array_equal(_run(drt, f), oracle_mod.drt2d_forward(f))
 
 
+@pytest.mark.parametrize("N", [32, 64, 128, 256])
+def test_uint8_single_cta_path(drt, oracle_mod, N):
+    """uint8 images with 32 <= N <= 256 run one CTA per (image, quadrant)
+    with 16-bit intermediates: full-range bytes (the largest sums) against
+    the oracle, and against the same images widened to int16 (multi-pass)."""
+    f = _imgs(N, 3, "u8", 800 + N)
+    f[0] = 255
+    got = _run(drt, f)
+    np.testing.assert_array_equal(got, oracle_mod.drt2d_forward(f))
+    np.testing.assert_array_equal(got, _run(drt, f.astype(np.int16)))
+
+
 @pytest.mark.parametrize("N", [4, 32, 128])
 def test_float_within_tree_rounding(drt, oracle_mod, N):
     """Each output is an n-level binary sum tree of N float32 terms, so its
@@ -64,12 +76,14 @@ def test_quadrant_subsets(drt, oracle_mod):
 @pytest.mark.parametrize("N", [32, 256])
 def test_chunked_batch(drt, oracle_mod, N):
     """A workspace that holds fewer images than the batch (a ragged last
-    chunk) gives the same result as the default one."""
+    chunk) gives the same result as the default one (int16 images: the
+    multi-pass path)."""
     B = 7
-    f = synth.images_2d(N, B, seed=11)
-    plan = drt.get_plan(N, torch.uint8)
+    f = synth.images_2d(N, B, seed=11).astype(np.int16)
+    plan = drt.get_plan(N, torch.int16)
     per = ctypes.c_size_t()
     plan._lib.drt2d_workspace_bytes(plan.handle, 1, 0xF, ctypes.byref(per))
+    assert per.value > 0
     ws = torch.empty(3 * per.value + 16, dtype=torch.uint8, device="cuda")  # 3 images per chunk
     got = _run(drt, f, workspace=ws)
     np.testing.assert_array_equal(got, oracle_mod.drt2d_forward(f))
@@ -121,10 +135,14 @@ def test_errors(drt):
     assert lib.drt2d_forward(plan.handle, img.data_ptr(), 2, out.data_ptr(), 0x10, None, 0, s) == 1
     assert lib.drt2d_forward(plan.handle, img.data_ptr() + 4, 2, out.data_ptr(), 0xF, None, 0, s) == 4
     assert lib.drt2d_forward(plan.handle, img.data_ptr(), -1, out.data_ptr(), 0xF, None, 0, s) == 1
-    big = drt.get_plan(64, torch.uint8)
-    img64 = torch.zeros((1, 64, 64), dtype=torch.uint8, device="cuda")
+    # int16 images of N = 64 go through the multi-pass path, which needs a workspace
+    big = drt.get_plan(64, torch.int16)
+    img64 = torch.zeros((1, 64, 64), dtype=torch.int16, device="cuda")
     out64 = torch.zeros((1, 4, 64, 128), dtype=torch.int32, device="cuda")
     assert lib.drt2d_forward(big.handle, img64.data_ptr(), 1, out64.data_ptr(), 0xF, None, 0, s) == 5
+    # uint8 images up to N = 256 need none (one CTA per image and quadrant)
+    u8 = drt.get_plan(64, torch.uint8)
+    assert lib.drt2d_forward(u8.handle, img64.data_ptr(), 1, out64.data_ptr(), 0xF, None, 0, s) == 0
     with pytest.raises(ValueError):
         drt.drt2d_forward(img, [4])
     assert abi.DRT3DError is not None
