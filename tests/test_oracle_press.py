@@ -137,3 +137,22 @@ def test_zero_padded_filter_breaks_convergence(press, monkeypatch):
     monkeypatch.setattr(press, "hfilter", zero_pad)
     hist = press.press_inverse(R, 15, steps, history=True)
     assert press.nrmsd(hist[-1], f) > 1e-2
+
+
+def test_fixed_point_is_the_least_squares_solution(press):
+    """The iteration converges to the unique solution of A f = R: at N = 4
+    it matches a dense least-squares solve with the 12-dodecant operator
+    (built column by column from the oracle's transform), which itself
+    returns f (A is injective)."""
+    N = 4
+    M = np.zeros((12 * N * N * 3 * N, N ** 3))
+    for i in range(N ** 3):
+        e = np.zeros(N ** 3)
+        e[i] = 1.0
+        M[:, i] = press.A(e.reshape(N, N, N)).ravel()
+    f = synth.random_float((N, N, N), 90).astype(np.float64)
+    R = press.A(f)
+    want = np.linalg.lstsq(M, R.ravel(), rcond=None)[0].reshape(N, N, N)
+    np.testing.assert_allclose(want, f, rtol=0, atol=1e-10)  # A is injective
+    got = press.press_inverse(R, 60, _steps(press, N))
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-9)
