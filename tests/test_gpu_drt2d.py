@@ -51,6 +51,8 @@ def test_uint8_single_cta_path(drt, oracle_mod, N):
     got = _run(drt, f)
     np.testing.assert_array_equal(got, oracle_mod.drt2d_forward(f))
     np.testing.assert_array_equal(got, _run(drt, f.astype(np.int16)))
+    for qs in ([3], [1, 2]):
+        np.testing.assert_array_equal(_run(drt, f, qs), got[:, qs])
 
 
 @pytest.mark.parametrize("N", [4, 32, 128])
