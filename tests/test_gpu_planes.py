@@ -156,6 +156,19 @@ def test_planes_global_layout_exact(drt, oracle_mod, N, dt):
     np.testing.assert_array_equal(got, oracle_mod.planes_global(f.astype(np.int32)))
 
 
+@pytest.mark.parametrize("N", [8, 32])
+def test_planes_global_layout_float(drt, oracle_mod, N):
+    """Float32 volumes: the global array against the oracle's float64
+    transform placed by Algorithm 2, per cell within the float32 bound used
+    for the dodecant outputs (1e-5 of the transform of |f|)."""
+    f = synth.random_float((N, N, N), 830 + N)
+    got = drt.planes_forward_global(torch.from_numpy(f).cuda()).cpu().numpy()
+    want = oracle_mod.place_global(oracle_mod.planes_forward(f.astype(np.float64)))
+    bound = 1e-5 * oracle_mod.place_global(oracle_mod.planes_forward(np.abs(f).astype(np.float64)))
+    assert got.dtype == np.float32 and got.shape == want.shape
+    assert (np.abs(got - want) <= bound + 1e-30).all()
+
+
 def test_planes_global_layout_n256_matches_dodecant_outputs(drt, oracle_mod):
     """At N = 256 (two fused passes, TMA-staged second pass) the global array
     is the 12 dodecant outputs placed by Algorithm 2 (the dodecant outputs
