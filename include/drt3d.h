@@ -17,6 +17,13 @@
  *    library allocates no device memory on any compute call; a plan owns only
  *    host metadata and one small device status word allocated at creation.
  *  - Device pointers must be 16-byte aligned.
+ *  - Compute calls may be made from several host threads at once, with one
+ *    plan or several, on any streams (drt3d_planes_forward_noalloc excepted:
+ *    its calls share one scratch array).  A plan's device status word is then
+ *    shared: an error recorded by one call is reported by whichever
+ *    drt3d_get_device_error() on that plan comes next.  Plan creation and
+ *    destruction, drt3d_plan_set_schedule and the profiling calls are not
+ *    thread-safe for the same plan.
  *  - N = 2^n with 2 <= N <= 1024 (Algorithms 1 and 3 take log2 N stages;
  *    non-cubic sizes are left as future work in the paper's conclusions).
  *  - Integer arithmetic is two's-complement int32 and wraps modulo 2^32, so

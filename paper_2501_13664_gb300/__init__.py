@@ -22,6 +22,7 @@ copied to the current CUDA device and the result copied back):
 from __future__ import annotations
 
 import ctypes
+import threading
 
 import torch
 
@@ -192,14 +193,16 @@ class BatchPlan:
 
 
 _plan_cache: dict = {}
+_plan_lock = threading.Lock()  # host threads may ask for the same plan at once
 
 
 def get_plan(N: int, dtype: torch.dtype) -> Plan:
     key = (torch.cuda.current_device(), int(N), dtype)
-    p = _plan_cache.get(key)
-    if p is None:
-        p = Plan(N, dtype)
-        _plan_cache[key] = p
+    with _plan_lock:
+        p = _plan_cache.get(key)
+        if p is None:
+            p = Plan(N, dtype)
+            _plan_cache[key] = p
     return p
 
 

@@ -396,10 +396,7 @@ drt3d_status drt3d_plan_create(drt3d_plan** plan, int N, drt3d_dtype in_dtype, u
 
 drt3d_status drt3d_plan_destroy(drt3d_plan* plan) {
     if (!plan) return DRT3D_OK;
-    for (drt3d_plan*& lp : plan->levels) {
-        drt3d_plan_destroy(lp);
-        lp = nullptr;
-    }
+    for (std::atomic<drt3d_plan*>& lp : plan->levels) drt3d_plan_destroy(lp.exchange(nullptr));
     if (plan->prof.events_made)
         for (int i = 0; i < 2 * kMaxLaunch; ++i) cudaEventDestroy(plan->prof.ev[i]);
     if (plan->d_status && !plan->borrowed_status) cudaFree(plan->d_status);
@@ -425,7 +422,8 @@ drt3d_status drt3d_lines_out_shape(const drt3d_plan* P, int64_t dims[5]) {
 // --------------------------------------------------------------------------
 static drt3d_plan* level_plan(const drt3d_plan* P, int l) {
     if (l == P->n) return const_cast<drt3d_plan*>(P);
-    if (!P->levels[l]) {
+    drt3d_plan* have = P->levels[l].load(std::memory_order_acquire);
+    if (!have) {
         drt3d_plan* q = new (std::nothrow) drt3d_plan();
         if (!q) return nullptr;
         q->N = 1 << l;
@@ -437,9 +435,11 @@ static drt3d_plan* level_plan(const drt3d_plan* P, int l) {
         q->borrowed_status = true;
         q->planes = make_planes_schedule(q->N);
         q->fused = make_fused_schedule(q->N, DRT3D_F32);
-        P->levels[l] = q;
+        if (P->levels[l].compare_exchange_strong(have, q, std::memory_order_acq_rel))
+            return q;
+        delete q;  // another thread installed the level first (`have` now holds it)
     }
-    return P->levels[l];
+    return have;
 }
 
 struct PressLayout {

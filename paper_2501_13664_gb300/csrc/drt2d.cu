@@ -288,13 +288,13 @@ cudaError_t launch_fused2(const Drt2dLaunch& L, int nslots, cudaStream_t s) {
     constexpr size_t smem = (size_t)N * P1 * 2;
     auto kern = drt2d_fused<G1, G2, NW>;
     if (smem > 48 * 1024) {
-        static unsigned long long attr_done = 0;  // one bit per device
+        static DeviceOnce attr_done;  // per instantiation
         int dev = 0;
         cudaGetDevice(&dev);
-        if (dev >= 64 || !((attr_done >> dev) & 1ull)) {
+        if (!attr_done.done(dev)) {
             const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            if (dev < 64) attr_done |= 1ull << dev;
+            attr_done.mark(dev);
         }
     }
     kern<<<(unsigned)nslots, NW * 32, smem, s>>>(L);

@@ -34,12 +34,24 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "drt3d.h"
 
 namespace drt3d {
 
 constexpr int kMaxN = 1024;
+
+// One flag per device (ordinals 0..63; higher ones never read as set), e.g.
+// "this kernel's dynamic shared-memory cap has been raised there".  Host
+// threads launching through the same plan may test and set it concurrently.
+struct DeviceOnce {
+    std::atomic<unsigned long long> bits{0};
+    bool done(int dev) const { return dev >= 0 && dev < 64 && ((bits.load(std::memory_order_acquire) >> dev) & 1ull); }
+    void mark(int dev) {
+        if (dev >= 0 && dev < 64) bits.fetch_or(1ull << dev, std::memory_order_release);
+    }
+};
 constexpr int kMaxSlots = 12;
 constexpr int kMaxPasses = 12;
 
@@ -313,7 +325,8 @@ struct drt3d_plan {
     drt3d::FusedSchedule fused;    // two-axis passes (forward)
     // Float32 plans of the coarser sizes N/2, N/4, ..., 2 used by the
     // iterative inverse, indexed by log2 of their size; host-only, created on
-    // first use, sharing this plan's status word.
-    mutable drt3d_plan* levels[11] = {};
+    // first use (by whichever host thread gets there first), sharing this
+    // plan's status word.
+    mutable std::atomic<drt3d_plan*> levels[11] = {};
     bool borrowed_status = false;
 };

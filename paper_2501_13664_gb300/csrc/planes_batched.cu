@@ -220,11 +220,11 @@ size_t batched_smem_bytes() { return ((size_t)(1 << 8) * fused_ws<4>() + K) * si
 // Opt the kernel into its shared-memory size once per device (done at bind,
 // so a launch inside stream capture issues only stream work).
 cudaError_t batched_prepare(int device) {
-    static unsigned long long done = 0;
-    if (device < 64 && ((done >> device) & 1ull)) return cudaSuccess;
+    static DeviceOnce done;
+    if (done.done(device)) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(planes_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)batched_smem_bytes());
-    if (e == cudaSuccess && device < 64) done |= 1ull << device;
+    if (e == cudaSuccess) done.mark(device);
     return e;
 }
 

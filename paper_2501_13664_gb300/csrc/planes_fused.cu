@@ -47,13 +47,13 @@ template <typename TIn, typename TOut, typename T, typename TS, int G, bool INGE
 cudaError_t launch_g(const FusedLaunch& L, int nslots, cudaStream_t s) {
     const size_t smem = ((size_t)(1 << (2 * G)) * fused_ws<G>() + K) * sizeof(TS);
     auto kern = planes_fused<TIn, TOut, T, TS, G, INGEST>;
-    static unsigned long long attr_done = 0;  // per instantiation, one bit per device
+    static DeviceOnce attr_done;  // per instantiation
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev >= 64 || !((attr_done >> dev) & 1ull)) {
+    if (!attr_done.done(dev)) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        if (dev < 64) attr_done |= 1ull << dev;
+        attr_done.mark(dev);
     }
     dim3 grid((unsigned)L.ctas, (unsigned)nslots);
     kern<<<grid, 32 * fused_warps<G>(), smem, s>>>(L);
@@ -78,13 +78,13 @@ template <typename TOut, int G>
 cudaError_t launch_tma_g(const FusedLaunch& L, const CUtensorMap& map, int nslots, cudaStream_t s) {
     const size_t smem = ((size_t)(1 << (2 * G)) * fused_ws<G>() + K) * 4 + 128;
     auto kern = planes_fused_tma<TOut, G>;
-    static unsigned long long attr_done = 0;  // per instantiation, one bit per device
+    static DeviceOnce attr_done;  // per instantiation
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev >= 64 || !((attr_done >> dev) & 1ull)) {
+    if (!attr_done.done(dev)) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        if (dev < 64) attr_done |= 1ull << dev;
+        attr_done.mark(dev);
     }
     dim3 grid((unsigned)L.ctas, (unsigned)nslots);
     kern<<<grid, 32 * fused_warps<G>(), smem, s>>>(L, map);

@@ -428,13 +428,13 @@ cudaError_t launch_inv_gc(const InvLaunch& L, cudaStream_t s) {
     auto kern = planes_inv_pass<G, CH, MULTI>;
     // The size cap is per device: raise it once to the device's opt-in
     // maximum (occupancy follows the size each launch asks for).
-    static unsigned long long attr_done = 0;  // one bit per device
-    static int optin_max[64] = {};
+    static DeviceOnce attr_done;
+    static std::atomic<int> optin_max[64] = {};  // written before the device's flag is set
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev >= 64) return cudaErrorInvalidDevice;
-    if (!((attr_done >> dev) & 1ull)) {
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_done.done(dev)) {
         int mx = 0;
         e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (e != cudaSuccess) return e;
@@ -444,10 +444,10 @@ cudaError_t launch_inv_gc(const InvLaunch& L, cudaStream_t s) {
         mx -= (int)fa.sharedSizeBytes;  // the cap counts dynamic memory only, beside the static
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         if (e != cudaSuccess) return e;
-        optin_max[dev] = mx;
-        attr_done |= 1ull << dev;
+        optin_max[dev].store(mx, std::memory_order_relaxed);
+        attr_done.mark(dev);
     }
-    if (smem > (size_t)optin_max[dev]) return cudaErrorInvalidValue;
+    if (smem > (size_t)optin_max[dev].load(std::memory_order_relaxed)) return cudaErrorInvalidValue;
     const unsigned units = (unsigned)((long long)L.N << (L.n - G));
     kern<<<units, inv_warps(G) * 32, smem, s>>>(L);
     return cudaGetLastError();
