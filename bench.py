@@ -685,8 +685,12 @@ def bench_lsq(drt3d, synth, dev) -> dict:
 
     step()
     t = sorted(_event_ms(step, 5))[2]
-    return {"ms_per_step": t, "volumes": B, "N": N,
-            "note": "forward (12 dodecants) + loss + hand-written adjoint via autograd, per step of 8 volumes"}
+    passes = profile_launches(drt3d.get_plan(N, torch.float32), step)
+    lib_ms = sum(e["ms"] for e in passes.values())
+    return {"ms_per_step": t, "volumes": B, "N": N, "passes": passes, "library_ms": lib_ms,
+            "note": "forward (12 dodecants) + loss + hand-written adjoint via autograd, per step of 8 volumes; "
+                    "passes = the library's launches of one step (the rest of the step is the loss and "
+                    "its gradient in PyTorch)"}
 
 
 def main(argv=None):

@@ -1,0 +1,139 @@
+// adjoint_sum.cu -- sum of the dodecants' backprojected frame volumes into
+// the volume (the last step of the planes adjoint, Section 5.1).
+//
+// One CTA owns a C^3 cube of the volume (C = min(16, N)).  A dodecant's map
+// is a signed permutation of the axes, so the cube's preimage in each frame
+// is again an aligned C^3 cube.  The CTA reads it with loads that run along
+// the frame's contiguous axis z', parks it in shared memory with padded
+// strides (1, C + 1, C (C + 1) + 1: odd, so a warp walking along any one frame
+// axis touches distinct banks), and every thread adds the elements of its
+// voxels, which run along the volume's contiguous axis z.  Frame i + 1's
+// cube is loaded into registers while frame i's is being added; the sum runs
+// in increasing i, the order in which the dodecants were selected.
+#include "adjoint_sum.cuh"
+
+#include <cstdlib>
+
+namespace drt3d {
+namespace {
+
+constexpr int kSumThreads = 256;
+
+// c[a] for a in {0, 1, 2} without a runtime-indexed array (kept in registers).
+__device__ __forceinline__ int pick(int a, int c0, int c1, int c2) { return a == 0 ? c0 : a == 1 ? c1 : c2; }
+
+template <int C>
+struct Cube {
+    static constexpr int V = C * C * C;                              // voxels
+    static constexpr int PER = (V + kSumThreads - 1) / kSumThreads;  // voxels per thread
+    static constexpr int SY = C + 1;                                 // padded shared-memory strides
+    static constexpr int SX = C * (C + 1) + 1;
+    static constexpr int WORDS = C * SX;
+};
+
+// Element e of a cube, local coordinates (e / C^2, (e / C) % C, e % C).
+template <typename T, int C>
+__global__ void __launch_bounds__(kSumThreads)
+frames_sum_kernel(const __grid_constant__ FramesSum S) {
+    using Q = Cube<C>;
+    __shared__ T cube[Q::WORDS];
+    const int N = S.N;
+    const int nc = N / C;  // cubes per axis
+    const int b = (int)blockIdx.x;
+    const int cx = (b / (nc * nc)) * C, cy = ((b / nc) % nc) * C, cz = (b % nc) * C;  // volume cube origin
+    const int t = (int)threadIdx.x;
+
+    T next[Q::PER];
+    auto load = [&](int i) {
+        const T* F = static_cast<const T*>(S.frame[i]);
+        // frame cube origin (ox, oy, oz)
+        const int vx = pick(S.vaxis[i][0], cx, cy, cz), vy = pick(S.vaxis[i][1], cx, cy, cz),
+                  vz = pick(S.vaxis[i][2], cx, cy, cz);
+        const int ox = S.flip[i][0] ? N - C - vx : vx, oy = S.flip[i][1] ? N - C - vy : vy,
+                  oz = S.flip[i][2] ? N - C - vz : vz;
+#pragma unroll
+        for (int r = 0; r < Q::PER; ++r) {
+            const int e = t + kSumThreads * r;
+            if (Q::V % kSumThreads == 0 || e < Q::V) {
+                const int x = e / (C * C), y = (e / C) % C, z = e % C;
+                next[r] = F[((long long)(ox + x) * N + (oy + y)) * N + (oz + z)];
+            }
+        }
+    };
+
+    T acc[Q::PER];
+    load(0);
+#pragma unroll 1
+    for (int i = 0; i < S.nslots; ++i) {
+#pragma unroll
+        for (int r = 0; r < Q::PER; ++r) {
+            const int e = t + kSumThreads * r;
+            if (Q::V % kSumThreads == 0 || e < Q::V) {
+                const int x = e / (C * C), y = (e / C) % C, z = e % C;
+                cube[x * Q::SX + y * Q::SY + z] = next[r];
+            }
+        }
+        __syncthreads();
+        if (i + 1 < S.nslots) load(i + 1);
+        // frame-local coordinates of each of the thread's volume-local voxels
+        const int ax0 = S.vaxis[i][0], ax1 = S.vaxis[i][1], ax2 = S.vaxis[i][2];
+        const bool f0 = S.flip[i][0], f1 = S.flip[i][1], f2 = S.flip[i][2];
+#pragma unroll
+        for (int r = 0; r < Q::PER; ++r) {
+            const int v = t + kSumThreads * r;
+            if (Q::V % kSumThreads == 0 || v < Q::V) {
+                const int x = v / (C * C), y = (v / C) % C, z = v % C;
+                const int p0 = pick(ax0, x, y, z), p1 = pick(ax1, x, y, z), p2 = pick(ax2, x, y, z);
+                const int l0 = f0 ? C - 1 - p0 : p0;
+                const int l1 = f1 ? C - 1 - p1 : p1;
+                const int l2 = f2 ? C - 1 - p2 : p2;
+                const T val = cube[l0 * Q::SX + l1 * Q::SY + l2];
+                acc[r] = i == 0 ? val : T(acc[r] + val);
+            }
+        }
+        __syncthreads();
+    }
+
+    T* vol = static_cast<T*>(S.vol);
+#pragma unroll
+    for (int r = 0; r < Q::PER; ++r) {
+        const int v = t + kSumThreads * r;
+        if (Q::V % kSumThreads == 0 || v < Q::V) {
+            const int x = v / (C * C), y = (v / C) % C, z = v % C;
+            vol[((long long)(cx + x) * N + (cy + y)) * N + (cz + z)] = acc[r];
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_t(const FramesSum& S, cudaStream_t s) {
+    const int C = S.N < 16 ? S.N : 16;
+    const int nc = S.N / C;
+    const unsigned blocks = (unsigned)nc * nc * nc;
+    switch (C) {
+    case 2: frames_sum_kernel<T, 2><<<blocks, kSumThreads, 0, s>>>(S); break;
+    case 4: frames_sum_kernel<T, 4><<<blocks, kSumThreads, 0, s>>>(S); break;
+    case 8: frames_sum_kernel<T, 8><<<blocks, kSumThreads, 0, s>>>(S); break;
+    case 16: frames_sum_kernel<T, 16><<<blocks, kSumThreads, 0, s>>>(S); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+void frames_sum_axes(const Affine& A, int N, int i, FramesSum* S) {
+    const long long st[3] = {A.sx, A.sy, A.sz};
+    for (int a = 0; a < 3; ++a) {
+        const long long m = std::llabs(st[a]);
+        S->vaxis[i][a] = (signed char)(m == 1 ? 2 : m == N ? 1 : 0);
+        S->flip[i][a] = (signed char)(st[a] < 0);
+    }
+}
+
+cudaError_t launch_frames_sum(const FramesSum& S, bool is_float, cudaStream_t s) {
+    if (S.nslots < 1 || S.nslots > kMaxSlots || S.N < 2 || (S.N & (S.N - 1))) return cudaErrorInvalidValue;
+    return is_float ? launch_t<float>(S, s) : launch_t<uint32_t>(S, s);
+}
+
+}  // namespace drt3d

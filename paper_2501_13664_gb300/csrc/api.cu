@@ -7,6 +7,7 @@
 #include <new>
 
 #include "internal.cuh"
+#include "adjoint_sum.cuh"
 
 namespace drt3d {
 
@@ -647,19 +648,16 @@ drt3d_status drt3d_planes_adjoint(const drt3d_plan* P, const void* d_cot, void* 
         const int span = 3 * N - e_lo + ((1 << ps.m0) - 1) * ((1 << ps.G) - 1);
         L.ntiles = (span + L.V - 1) / L.V;
         L.warps = ((long long)N << (P->n - ps.G)) * L.ntiles;
-        auto fill = [&](int i, int k) {
+        auto fill = [&](int i) {
             char* bufA = ws + (size_t)i * 2 * buf;
             char* bufB = bufA + buf;
-            SlotPtrs& sp = L.slot[0 + (p == 0 ? 0 : i)];
-            sp.map = dodecant_affine(N, k);
+            SlotPtrs& sp = L.slot[i];
             sp.in = (q == 0) ? (const void*)(static_cast<const char*>(d_cot) + (size_t)i * cot_block)
                              : ((q & 1) ? (const void*)bufA : (const void*)bufB);
-            sp.out = (p == 0) ? d_vol : ((q & 1) ? (void*)bufB : (void*)bufA);
+            sp.out = (q & 1) ? (void*)bufB : (void*)bufA;
         };
         if (p > 0) {
-            int i = 0;
-            for (int k = 0; k < 12; ++k)
-                if ((mask >> k) & 1) fill(i++, k);
+            for (int i = 0; i < nslots; ++i) fill(i);
             L.accumulate = 0;
             char nm[40];
             std::snprintf(nm, sizeof nm, "planes_adj_pass %c G=%d m0=%d", ps.axis ? 'y' : 'x', ps.G, ps.m0);
@@ -668,19 +666,31 @@ drt3d_status drt3d_planes_adjoint(const drt3d_plan* P, const void* d_cot, void* 
                 return DRT3D_ERR_CUDA;
             prof_end(P, stream);
         } else {
-            // Scatter into the volume one dodecant at a time, in increasing k,
-            // so the sum over dodecants has a fixed order.
-            int i = 0;
-            for (int k = 0; k < 12; ++k) {
+            // Every dodecant's frame volume F_k[x'][y'][z'] (rows d in [2N, 3N))
+            // into the buffer this pass does not read, in one launch; then their
+            // sum through the dodecant maps, added in increasing k so that the
+            // float sum has a fixed order.
+            FramesSum FS{};
+            for (int k = 0, i = 0; k < 12; ++k) {
                 if (!((mask >> k) & 1)) continue;
-                fill(i, k);
-                L.accumulate = (i > 0);
-                prof_begin(P, stream, "planes_adj_scatter", planes_pass_bytes(P, ps, 0, 0, true));
-                if (launch_planes_adjoint_pass(L, ps.G, true, is_float, 1, stream) != cudaSuccess)
-                    return DRT3D_ERR_CUDA;
-                prof_end(P, stream);
+                fill(i);
+                L.slot[i].map = Affine{0, (long long)N * N, (long long)N, 1};  // the frame itself
+                FS.frame[i] = L.slot[i].out;
+                frames_sum_axes(dodecant_affine(N, k), N, i, &FS);
                 ++i;
             }
+            L.accumulate = 0;
+            prof_begin(P, stream, "planes_adj_frames", nslots * planes_pass_bytes(P, ps, 0, 0, true));
+            if (launch_planes_adjoint_pass(L, ps.G, true, is_float, nslots, stream) != cudaSuccess)
+                return DRT3D_ERR_CUDA;
+            prof_end(P, stream);
+            FS.vol = d_vol;
+            FS.N = N;
+            FS.nslots = nslots;
+            const double vox = (double)N * N * N * 4;
+            prof_begin(P, stream, "planes_adj_sum", (nslots + 1) * vox);
+            if (launch_frames_sum(FS, is_float, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+            prof_end(P, stream);
         }
     }
     return DRT3D_OK;

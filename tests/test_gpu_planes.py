@@ -95,11 +95,23 @@ def test_forward_float_within_tolerance(drt, oracle_mod, N):
     assert np.all(np.abs(got - ref) <= FTOL * mag + 1e-30)
 
 
-@pytest.mark.parametrize("N", [2, 8, 32])
+@pytest.mark.parametrize("N", [2, 4, 8, 32, 128])
 def test_adjoint_integer_exact(drt, oracle_mod, N):
     r = synth.random_int32((12, N, N, 3 * N), 11)
     got = drt.planes_adjoint(torch.from_numpy(r).cuda()).cpu().numpy()
     np.testing.assert_array_equal(got, oracle_mod.planes_adjoint(r))
+
+
+@pytest.mark.parametrize("N", [4, 64])
+def test_adjoint_ignores_stale_workspace(drt, oracle_mod, N):
+    """Every dodecant's frame volume is written in full before the frames are
+    summed: a workspace full of garbage gives the oracle's result."""
+    ks = [0, 5, 6, 11]
+    r = synth.random_int32((len(ks), N, N, 3 * N), 15)
+    plan = drt.get_plan(N, torch.int32)
+    ws = torch.full((plan.workspace_bytes("planes_adjoint"),), 0xA5, dtype=torch.uint8, device="cuda")
+    got = drt.planes_adjoint(torch.from_numpy(r).cuda(), ks, workspace=ws).cpu().numpy()
+    np.testing.assert_array_equal(got, oracle_mod.planes_adjoint(r, ks))
 
 
 def test_adjoint_subset_order(drt, oracle_mod):
