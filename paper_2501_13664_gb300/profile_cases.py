@@ -21,6 +21,8 @@ on the device at most.
                     (134 MB of int32 out)
     press-n64       N=64 float32 phantom, two iterations of the multigrid
                     inverse (step sizes from the power iteration first)
+    adj-f32-n128    N=128 float32 cotangent of all 12 dodecants (302 MB),
+                    planes adjoint (backprojection) to the volume
 """
 from __future__ import annotations
 
@@ -36,15 +38,15 @@ def _sched(s: str):
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("case", choices=["fused-n256-d1", "fused-n256", "inverse-n256", "lines-n64-s0", "batched-c4-n64",
-                                     "lines-adj-n64", "drt2d-n256", "press-n64"])
+                                     "lines-adj-n64", "drt2d-n256", "press-n64", "adj-f32-n128"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--schedule", type=str, default="4,4", help="stage-fusion split of the N=256 planes cases")
     args = ap.parse_args(argv)
 
     import synth
 
-    from . import (ALL, BatchPlan, drt2d_forward, get_plan, lines_adjoint, lines_forward, planes_forward,
-                   planes_inverse, planes_press_inverse, press_step_sizes)
+    from . import (ALL, BatchPlan, drt2d_forward, get_plan, lines_adjoint, lines_forward, planes_adjoint,
+                   planes_forward, planes_inverse, planes_press_inverse, press_step_sizes)
 
     dev = torch.device("cuda", 0)
     sched = _sched(args.schedule)
@@ -105,6 +107,17 @@ def main(argv=None) -> int:
         torch.cuda.synchronize()
         err = float(torch.sqrt(torch.mean((out - f) ** 2)) / (f.max() - f.min()))
         print(f"{args.case}: reps={args.reps} nrmsd={err:.3e}")
+    elif args.case == "adj-f32-n128":
+        N = 128
+        cot = torch.from_numpy(synth.random_float((12, N, N, 3 * N), 16)).to(dev)
+        plan = get_plan(N, torch.float32)
+        ws = plan.workspace("planes_adjoint")
+        back = torch.empty((N, N, N), dtype=torch.float32, device=dev)
+        for _ in range(args.reps):
+            planes_adjoint(cot, ALL, out=back, workspace=ws)
+        torch.cuda.synchronize()
+        status = plan.device_error()
+        print(f"{args.case}: reps={args.reps} status={status} sum={float(back.double().sum()):.6e}")
     elif args.case == "lines-n64-s0":
         N = 64
         vol = torch.from_numpy(synth.c3_volume(N)).to(dev)
