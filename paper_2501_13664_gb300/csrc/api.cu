@@ -658,11 +658,10 @@ drt3d_status drt3d_planes_adjoint(const drt3d_plan* P, const void* d_cot, void* 
         };
         if (p > 0) {
             for (int i = 0; i < nslots; ++i) fill(i);
-            L.accumulate = 0;
             char nm[40];
             std::snprintf(nm, sizeof nm, "planes_adj_pass %c G=%d m0=%d", ps.axis ? 'y' : 'x', ps.G, ps.m0);
             prof_begin(P, stream, nm, nslots * planes_pass_bytes(P, ps, mxs[p], mys[p], true));
-            if (launch_planes_adjoint_pass(L, ps.G, false, is_float, nslots, stream) != cudaSuccess)
+            if (launch_planes_adjoint_pass(L, ps.G, is_float, nslots, stream) != cudaSuccess)
                 return DRT3D_ERR_CUDA;
             prof_end(P, stream);
         } else {
@@ -674,14 +673,13 @@ drt3d_status drt3d_planes_adjoint(const drt3d_plan* P, const void* d_cot, void* 
             for (int k = 0, i = 0; k < 12; ++k) {
                 if (!((mask >> k) & 1)) continue;
                 fill(i);
-                L.slot[i].map = Affine{0, (long long)N * N, (long long)N, 1};  // the frame itself
                 FS.frame[i] = L.slot[i].out;
                 frames_sum_axes(dodecant_affine(N, k), N, i, &FS);
                 ++i;
             }
-            L.accumulate = 0;
+            L.gin = Geo{2 * N, N};  // rows d in [2N, 3N), pitch N: the frame F[x'][y'][z']
             prof_begin(P, stream, "planes_adj_frames", nslots * planes_pass_bytes(P, ps, 0, 0, true));
-            if (launch_planes_adjoint_pass(L, ps.G, true, is_float, nslots, stream) != cudaSuccess)
+            if (launch_planes_adjoint_pass(L, ps.G, is_float, nslots, stream) != cudaSuccess)
                 return DRT3D_ERR_CUDA;
             prof_end(P, stream);
             FS.vol = d_vol;

@@ -116,7 +116,6 @@ struct PassLaunch {
     int V;                // valid outputs per warp tile
     int ntiles;           // warp tiles along d
     long long warps;      // warps per slot
-    int accumulate;       // adjoint scatter: 0 = store, 1 = add
 };
 
 // Element type of a buffer read or written by a fused pass.
@@ -296,8 +295,7 @@ cudaError_t encode_fused_tmap(const FusedLaunch& L, const void* in_base, size_t 
                               CUtensorMap* map);
 cudaError_t launch_planes_pass(const PassLaunch& L, int G, drt3d_dtype in_dtype, bool ingest,
                                bool is_float, int nslots, cudaStream_t s);
-cudaError_t launch_planes_adjoint_pass(const PassLaunch& L, int G, bool scatter, bool is_float,
-                                       int nslots, cudaStream_t s);
+cudaError_t launch_planes_adjoint_pass(const PassLaunch& L, int G, bool is_float, int nslots, cudaStream_t s);
 
 }  // namespace drt3d
 

@@ -11,8 +11,10 @@
 // Adjoint pass (Section 5.1: the stage loop reversed with
 // eq.(invmap3Dsummation)): the transpose of the forward pass.  It loads the
 // unit's 2^G cotangent rows unsheared, runs the transposed register
-// transform and stores row u shifted by sg * u; the transpose of the first
-// pass scatters into the volume through the dodecant map.
+// transform and stores row u shifted by sg * u.  The transpose of the first
+// pass writes rows d in [2N, 3N) only: given the row geometry (base 2N,
+// pitch N) it writes the dodecant's frame volume F[x'][y'][z'], which the
+// caller then sums over the dodecants through their maps.
 #include <type_traits>
 
 #include "internal.cuh"
@@ -100,8 +102,9 @@ planes_fwd_pass(const __grid_constant__ PassLaunch L) {
 // Transpose of planes_fwd_pass.  Tile positions p are in the cotangent's
 // (output) frame; row u's result at p belongs to displacement
 // d0 + p + sg * u of the input frame.  Valid positions are
-// p in [2^G - 1, 2^G - 1 + V).
-template <typename T, int G, bool SCATTER>
+// p in [2^G - 1, 2^G - 1 + V).  The input-frame rows produced are
+// d in [gin.base, 3N).
+template <typename T, int G>
 __global__ void __launch_bounds__(kWarps * 32)
 planes_adj_pass(const __grid_constant__ PassLaunch L) {
     constexpr int K = kK;
@@ -120,7 +123,7 @@ planes_adj_pass(const __grid_constant__ PassLaunch L) {
     const int j = (int)(unit >> wb);
     const int N = L.N;
     // Input-frame range this pass must produce.
-    const int e_lo = SCATTER ? 2 * N : L.gin.base;
+    const int e_lo = L.gin.base;
     // Tiles start low enough that row R-1 (shifted by sg*(R-1)) still
     // reaches e_lo: d0 = e_lo - P0 - sg_max*(R-1) + tile*V.
     const int sg_max = (1 << L.m0) - 1;
@@ -153,20 +156,9 @@ planes_adj_pass(const __grid_constant__ PassLaunch L) {
             const int p = lane * K + i;
             const int e = d0 + p + sg * u;
             const bool ok = p >= P0 && p < P0 + L.V && e >= e_lo && e < L.dmax;
-            if constexpr (SCATTER) {
-                const int xp = L.axis == 0 ? a : j;
-                const int yp = L.axis == 0 ? j : a;
-                T* vol = static_cast<T*>(sp.out);
-                if (ok) {
-                    const long long idx = sp.map.o0 + xp * sp.map.sx + yp * sp.map.sy +
-                                          (long long)(e - 2 * N) * sp.map.sz;
-                    vol[idx] = L.accumulate ? T(vol[idx] + v[u][i]) : v[u][i];
-                }
-            } else {
-                T* buf = static_cast<T*>(sp.out);
-                const long long row = L.axis == 0 ? ((long long)a * N + j) : ((long long)j * N + a);
-                if (ok) buf[row * L.gin.pitch + (e - L.gin.base)] = v[u][i];
-            }
+            T* buf = static_cast<T*>(sp.out);
+            const long long row = L.axis == 0 ? ((long long)a * N + j) : ((long long)j * N + a);
+            if (ok) buf[row * L.gin.pitch + (e - L.gin.base)] = v[u][i];
         }
     }
 }
@@ -185,15 +177,15 @@ cudaError_t fwd_dispatch(const PassLaunch& L, int G, int nslots, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <typename T, bool SCATTER>
+template <typename T>
 cudaError_t adj_dispatch(const PassLaunch& L, int G, int nslots, cudaStream_t s) {
     const long long blocks = (L.warps + kWarps - 1) / kWarps;
     dim3 grid((unsigned)blocks, (unsigned)nslots);
     switch (G) {
-    case 1: planes_adj_pass<T, 1, SCATTER><<<grid, kWarps * 32, 0, s>>>(L); break;
-    case 2: planes_adj_pass<T, 2, SCATTER><<<grid, kWarps * 32, 0, s>>>(L); break;
-    case 3: planes_adj_pass<T, 3, SCATTER><<<grid, kWarps * 32, 0, s>>>(L); break;
-    case 4: planes_adj_pass<T, 4, SCATTER><<<grid, kWarps * 32, 0, s>>>(L); break;
+    case 1: planes_adj_pass<T, 1><<<grid, kWarps * 32, 0, s>>>(L); break;
+    case 2: planes_adj_pass<T, 2><<<grid, kWarps * 32, 0, s>>>(L); break;
+    case 3: planes_adj_pass<T, 3><<<grid, kWarps * 32, 0, s>>>(L); break;
+    case 4: planes_adj_pass<T, 4><<<grid, kWarps * 32, 0, s>>>(L); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -218,13 +210,8 @@ cudaError_t launch_planes_pass(const PassLaunch& L, int G, drt3d_dtype in_dtype,
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_planes_adjoint_pass(const PassLaunch& L, int G, bool scatter, bool is_float,
-                                       int nslots, cudaStream_t s) {
-    if (scatter)
-        return is_float ? adj_dispatch<float, true>(L, G, nslots, s)
-                        : adj_dispatch<uint32_t, true>(L, G, nslots, s);
-    return is_float ? adj_dispatch<float, false>(L, G, nslots, s)
-                    : adj_dispatch<uint32_t, false>(L, G, nslots, s);
+cudaError_t launch_planes_adjoint_pass(const PassLaunch& L, int G, bool is_float, int nslots, cudaStream_t s) {
+    return is_float ? adj_dispatch<float>(L, G, nslots, s) : adj_dispatch<uint32_t>(L, G, nslots, s);
 }
 
 }  // namespace drt3d
