@@ -35,6 +35,15 @@ __device__ __forceinline__ T to_acc(TIn x) {
     }
 }
 
+template <typename T>
+__device__ __forceinline__ T from_bits(uint32_t x) {
+    if constexpr (std::is_same<T, float>::value) {
+        return __uint_as_float(x);
+    } else {
+        return (T)x;
+    }
+}
+
 template <typename TIn, typename T, int G, bool INGEST>
 __global__ void __launch_bounds__(kWarps * 32)
 planes_fwd_pass(const __grid_constant__ PassLaunch L) {
@@ -134,15 +143,27 @@ planes_adj_pass(const __grid_constant__ PassLaunch L) {
 
     T v[R][K];
     const T* cot = static_cast<const T*>(sp.in);
+    static_assert(K == 4, "one 16-byte vector per lane and row");
 #pragma unroll
     for (int t = 0; t < R; ++t) {
         const int o = t + (sg << G) + (wq << (L.m0 + G));
         const long long row = L.axis == 0 ? ((long long)o * N + j) : ((long long)j * N + o);
-        const long long rbase = row * L.gout.pitch - L.gout.base;
+        const T* rp = cot + (row * L.gout.pitch - L.gout.base);  // element d of the row at rp[d]
+        // A lane's four elements lie inside the stored row and start on a
+        // 16-byte boundary whenever the tile origin is a multiple of 4 (m0 >= 2):
+        // one vector load; otherwise element by element.
+        if (pos0 >= L.gout.base && pos0 + K <= L.dmax && (reinterpret_cast<uintptr_t>(rp + pos0) & 15u) == 0) {
+            const uint4 w = __ldg(reinterpret_cast<const uint4*>(rp + pos0));
+            v[t][0] = from_bits<T>(w.x);
+            v[t][1] = from_bits<T>(w.y);
+            v[t][2] = from_bits<T>(w.z);
+            v[t][3] = from_bits<T>(w.w);
+        } else {
 #pragma unroll
-        for (int i = 0; i < K; ++i) {
-            const int d = pos0 + i;
-            v[t][i] = (d >= L.gout.base && d < L.dmax) ? cot[rbase + d] : T(0);
+            for (int i = 0; i < K; ++i) {
+                const int d = pos0 + i;
+                v[t][i] = (d >= L.gout.base && d < L.dmax) ? rp[d] : T(0);
+            }
         }
     }
 
