@@ -17,6 +17,10 @@
  *    library allocates no device memory on any compute call; a plan owns only
  *    host metadata and one small device status word allocated at creation.
  *  - Device pointers must be 16-byte aligned.
+ *  - A plan (and a batch plan) belongs to the device that was current when
+ *    it was created.  Compute calls and status reads must be made with that
+ *    device current; otherwise they return DRT3D_ERR_INVALID_ARG and enqueue
+ *    nothing.
  *  - Compute calls may be made from several host threads at once, with one
  *    plan or several, on any streams (drt3d_planes_forward_noalloc excepted:
  *    its calls share one scratch array).  A plan's device status word is then

@@ -535,6 +535,7 @@ static void global_row_map(int N, int k, FusedSlot& fs) {
 static drt3d_status planes_forward_impl(const drt3d_plan* P, const void* d_in, void* d_out, uint32_t mask,
                                         void* d_ws, size_t ws_bytes, cudaStream_t stream, bool global) {
     if (!P || !d_in || !d_out) return DRT3D_ERR_INVALID_ARG;
+    if (!device_is_current(P->device)) return DRT3D_ERR_INVALID_ARG;
     if (mask == 0 || (mask & ~DRT3D_ALL_DODECANTS)) return DRT3D_ERR_INVALID_ARG;
     if (!aligned16(d_in) || !aligned16(d_out) || !aligned16(d_ws)) return DRT3D_ERR_ALIGN;
     const FusedSchedule& S = P->fused;
@@ -596,6 +597,7 @@ drt3d_status drt3d_planes_forward(const drt3d_plan* P, const void* d_in, void* d
 drt3d_status drt3d_planes_forward_global(const drt3d_plan* P, const void* d_in, void* d_out, void* d_ws,
                                          size_t ws_bytes, cudaStream_t stream) {
     if (!P || !d_in || !d_out) return DRT3D_ERR_INVALID_ARG;
+    if (!device_is_current(P->device)) return DRT3D_ERR_INVALID_ARG;
     if (P->N < 4) return DRT3D_ERR_SIZE;
     if (!aligned16(d_out)) return DRT3D_ERR_ALIGN;
     const int N = P->N;
@@ -613,6 +615,7 @@ drt3d_status drt3d_planes_forward_global(const drt3d_plan* P, const void* d_in, 
 drt3d_status drt3d_planes_adjoint(const drt3d_plan* P, const void* d_cot, void* d_vol, uint32_t mask,
                                   void* d_ws, size_t ws_bytes, cudaStream_t stream) {
     if (!P || !d_cot || !d_vol) return DRT3D_ERR_INVALID_ARG;
+    if (!device_is_current(P->device)) return DRT3D_ERR_INVALID_ARG;
     if (P->dtype != DRT3D_I32 && P->dtype != DRT3D_F32) return DRT3D_ERR_DTYPE;
     if (mask == 0 || (mask & ~DRT3D_ALL_DODECANTS)) return DRT3D_ERR_INVALID_ARG;
     if (!aligned16(d_cot) || !aligned16(d_vol) || !aligned16(d_ws)) return DRT3D_ERR_ALIGN;
@@ -697,6 +700,7 @@ drt3d_status drt3d_planes_adjoint(const drt3d_plan* P, const void* d_cot, void* 
 drt3d_status drt3d_planes_inverse(const drt3d_plan* P, const int32_t* d_R, int dodecant, int32_t* d_vol,
                                   void* d_ws, size_t ws_bytes, cudaStream_t stream) {
     if (!P || !d_R || !d_vol) return DRT3D_ERR_INVALID_ARG;
+    if (!device_is_current(P->device)) return DRT3D_ERR_INVALID_ARG;
     if (dodecant < 0 || dodecant >= 12) return DRT3D_ERR_INVALID_ARG;
     if (P->dtype == DRT3D_F32) return DRT3D_ERR_DTYPE;
     if (!aligned16(d_R) || !aligned16(d_vol) || !aligned16(d_ws)) return DRT3D_ERR_ALIGN;
@@ -736,6 +740,7 @@ drt3d_status drt3d_planes_inverse(const drt3d_plan* P, const int32_t* d_R, int d
 drt3d_status djt3d_lines_forward(const drt3d_plan* P, const void* d_in, int32_t* d_out, uint32_t mask,
                                  void* d_ws, size_t ws_bytes, cudaStream_t stream) {
     if (!P || !d_in || !d_out) return DRT3D_ERR_INVALID_ARG;
+    if (!device_is_current(P->device)) return DRT3D_ERR_INVALID_ARG;
     if (mask == 0 || (mask & ~DRT3D_ALL_SECTORS)) return DRT3D_ERR_INVALID_ARG;
     if (P->dtype == DRT3D_F32) return DRT3D_ERR_DTYPE;
     if (P->N > 256) return DRT3D_ERR_SIZE;
@@ -822,6 +827,7 @@ drt3d_status djt3d_lines_forward(const drt3d_plan* P, const void* d_in, int32_t*
 drt3d_status djt3d_lines_adjoint(const drt3d_plan* P, const int32_t* d_cot, int32_t* d_vol, uint32_t mask,
                                  void* d_ws, size_t ws_bytes, cudaStream_t stream) {
     if (!P || !d_cot || !d_vol) return DRT3D_ERR_INVALID_ARG;
+    if (!device_is_current(P->device)) return DRT3D_ERR_INVALID_ARG;
     if (mask == 0 || (mask & ~DRT3D_ALL_SECTORS)) return DRT3D_ERR_INVALID_ARG;
     if (P->dtype != DRT3D_I32) return DRT3D_ERR_DTYPE;
     if (P->N > 256) return DRT3D_ERR_SIZE;
@@ -914,6 +920,7 @@ drt3d_status drt3d_planes_press_inverse(const drt3d_plan* P, const float* d_R, f
                                         int smooth, const float* steps, void* d_ws, size_t ws_bytes,
                                         cudaStream_t stream) {
     if (!P || !d_R || !d_vol || !steps || iterations < 0 || smooth < 1) return DRT3D_ERR_INVALID_ARG;
+    if (!device_is_current(P->device)) return DRT3D_ERR_INVALID_ARG;
     if (!aligned16(d_R) || !aligned16(d_vol)) return DRT3D_ERR_ALIGN;
     drt3d_status st;
     if (!press_args_ok(P, d_ws, ws_bytes, &st)) return st;
@@ -960,6 +967,7 @@ drt3d_status drt3d_planes_press_inverse(const drt3d_plan* P, const float* d_R, f
 drt3d_status drt3d_press_spectral_radius(const drt3d_plan* P, int level, const float* d_start, int iterations,
                                          double* lambda, void* d_ws, size_t ws_bytes, cudaStream_t stream) {
     if (!P || !d_start || !lambda || iterations < 1 || level < 1 || level > P->n) return DRT3D_ERR_INVALID_ARG;
+    if (!device_is_current(P->device)) return DRT3D_ERR_INVALID_ARG;
     if (!aligned16(d_start)) return DRT3D_ERR_ALIGN;
     drt3d_status st;
     if (!press_args_ok(P, d_ws, ws_bytes, &st)) return st;
@@ -1007,6 +1015,7 @@ drt3d_status drt2d_workspace_bytes(const drt3d_plan* P, int B, uint32_t qmask, s
 drt3d_status drt2d_forward(const drt3d_plan* P, const void* d_img, int B, void* d_out, uint32_t qmask, void* d_ws,
                            size_t ws_bytes, cudaStream_t stream) {
     if (!P || B < 0 || qmask == 0 || (qmask & ~DRT2D_ALL_QUADRANTS)) return DRT3D_ERR_INVALID_ARG;
+    if (!device_is_current(P->device)) return DRT3D_ERR_INVALID_ARG;
     if (B == 0) return DRT3D_OK;
     if (!d_img || !d_out) return DRT3D_ERR_INVALID_ARG;
     if (!aligned16(d_img) || !aligned16(d_out) || !aligned16(d_ws)) return DRT3D_ERR_ALIGN;
@@ -1125,6 +1134,7 @@ const char* drt3d_profiled_launch_name(const drt3d_plan* P, int i) {
 
 drt3d_status drt3d_get_device_error(const drt3d_plan* P, cudaStream_t stream) {
     if (!P) return DRT3D_ERR_INVALID_ARG;
+    if (!drt3d::device_is_current(P->device)) return DRT3D_ERR_INVALID_ARG;
     if (cudaStreamSynchronize(stream) != cudaSuccess) return DRT3D_ERR_CUDA;
     int h = 0;
     if (cudaMemcpy(&h, P->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return DRT3D_ERR_CUDA;

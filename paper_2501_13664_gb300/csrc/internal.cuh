@@ -52,6 +52,14 @@ struct DeviceOnce {
         if (dev >= 0 && dev < 64) bits.fetch_or(1ull << dev, std::memory_order_release);
     }
 };
+// Whether `device` is the calling thread's current device: a plan's status
+// word and the tables its launches read live there, so compute calls made
+// with another device current are rejected as an argument error.
+inline bool device_is_current(int device) {
+    int cur = -1;
+    return cudaGetDevice(&cur) == cudaSuccess && cur == device;
+}
+
 constexpr int kMaxSlots = 12;
 constexpr int kMaxPasses = 12;
 

@@ -66,6 +66,8 @@ size_t drt3d_noalloc_scratch_bytes(void) { return kNoallocScratchBytes; }
 drt3d_status drt3d_planes_forward_noalloc(const drt3d_plan* plan, const void* d_in, void* d_out,
                                           uint32_t dodecant_mask, cudaStream_t stream) {
     if (!plan || !d_in || !d_out) return DRT3D_ERR_INVALID_ARG;
+    // The scratch address below is the current device's: it must be the plan's.
+    if (!drt3d::device_is_current(plan->device)) return DRT3D_ERR_INVALID_ARG;
     if (dodecant_mask == 0 || (dodecant_mask & ~DRT3D_ALL_DODECANTS)) return DRT3D_ERR_INVALID_ARG;
     // Scratch this call needs: two intermediate buffers per selected
     // dodecant (none when the schedule is a single pass).

@@ -383,6 +383,7 @@ drt3d_status drt3d_batch_workspace_bytes(const drt3d_batch_plan* B, size_t* byte
 
 drt3d_status drt3d_batch_bind(drt3d_batch_plan* B, const drt3d_vol_desc* descs, void* d_ws, size_t ws_bytes) {
     if (!B || !descs) return DRT3D_ERR_INVALID_ARG;
+    if (!device_is_current(B->device)) return DRT3D_ERR_INVALID_ARG;
     size_t need = 0;
     drt3d_batch_workspace_bytes(B, &need);
     if (need > 0 && (!d_ws || ws_bytes < need)) return DRT3D_ERR_WORKSPACE;
@@ -509,6 +510,7 @@ drt3d_status drt3d_batch_set_mode(drt3d_batch_plan* B, int mode, int nstreams) {
 
 drt3d_status drt3d_planes_forward_batched(const drt3d_batch_plan* B, cudaStream_t stream) {
     if (!B || !B->bound) return DRT3D_ERR_INVALID_ARG;
+    if (!device_is_current(B->device)) return DRT3D_ERR_INVALID_ARG;
     if (B->mode == 1) {
         // pass-major over the volumes; a volume's passes stay on its stream
         if (cudaEventRecord(B->fork, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
@@ -559,6 +561,7 @@ drt3d_status drt3d_planes_forward_batched(const drt3d_batch_plan* B, cudaStream_
 
 drt3d_status drt3d_batch_get_device_error(const drt3d_batch_plan* B, cudaStream_t stream) {
     if (!B) return DRT3D_ERR_INVALID_ARG;
+    if (!device_is_current(B->device)) return DRT3D_ERR_INVALID_ARG;
     if (cudaStreamSynchronize(stream) != cudaSuccess) return DRT3D_ERR_CUDA;
     int h = 0;
     if (cudaMemcpy(&h, B->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return DRT3D_ERR_CUDA;

@@ -32,6 +32,8 @@ Workloads (numpy ``default_rng(seed)`` throughout):
                      MRI inversions (the scans themselves are not available).
 * ``dense_u8``    -- N^3 uint8 uniform 0..255, drawn directly as bytes (the
                      maximum-size tests, N up to 1024).
+* ``raw_int32``   -- full-range uniform int32 from the generator's raw bits
+                     (multi-GB lines cotangents at N = 128).
 """
 from __future__ import annotations
 
@@ -157,6 +159,15 @@ def random_int32(shape, seed: int, lo: int = -(2 ** 31), hi: int = 2 ** 31) -> n
     """Uniform int32 over [lo, hi) (full range by default, exercises wrapping)."""
     rng = np.random.default_rng(seed)
     return rng.integers(lo, hi, size=shape, dtype=np.int64).astype(np.int32)
+
+
+def raw_int32(shape, seed: int) -> np.ndarray:
+    """Uniform int32 over the full range, taken straight from the generator's
+    raw 64-bit output (fast enough for multi-GB cotangents)."""
+    n = int(np.prod(shape))
+    rng = np.random.default_rng(seed)
+    raw = rng.bit_generator.random_raw((n + 1) // 2)
+    return raw.view(np.int32)[:n].reshape(shape)
 
 
 def random_float(shape, seed: int) -> np.ndarray:

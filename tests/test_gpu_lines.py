@@ -64,8 +64,8 @@ def test_lines_n64_selected_sectors(drt, oracle_mod):
 def test_config_c3_full_size(drt, oracle_mod):
     """N = 128 int16 volume with 32 embedded lines, all 12 sectors (51.5 GB of
     output): mass per slope pair, empty displacement row/column 0, and 10^5
-    random cells against the eq.(3DfDJT) definition; sector 0 in full
-    against Algorithm 3."""
+    random cells against the eq.(3DfDJT) definition; an x-, a y- and a
+    z-driven sector (0, 6, 11) in full against Algorithm 3."""
     N = 128
     f = synth.c3_volume(N)
     J = drt.lines_forward(torch.from_numpy(f).cuda())
@@ -84,7 +84,8 @@ def test_config_c3_full_size(drt, oracle_mod):
         got = J[k][it[:, 0], it[:, 1], it[:, 2], it[:, 3]].cpu().numpy()
         for (a, b, c, d), v in zip(idx, got):
             assert oracle_mod.lines_cell(g, int(a), int(b), int(c), int(d)) == int(v)
-    np.testing.assert_array_equal(J[0].cpu().numpy(), oracle_mod.lines_forward(f, [0])[0])
+    for k in (0, 6, 11):
+        np.testing.assert_array_equal(J[k].cpu().numpy(), oracle_mod.lines_forward(f, [k])[0], err_msg=f"sector {k}")
 
 
 # ---------------------------------------------------------------------------
@@ -113,6 +114,18 @@ def test_lines_adjoint_n64_selected_sectors(drt, oracle_mod):
     sel = [3, 8]
     r = synth.random_int32((2, N, N, 2 * N, 2 * N), 720)
     np.testing.assert_array_equal(_adj(drt, r, sel), oracle_mod.lines_adjoint(r, sel))
+
+
+@pytest.mark.parametrize("k", [2, 5, 9])  # x-, y- and z-driven
+def test_lines_adjoint_n128_full_sector(drt, oracle_mod, k):
+    """Config-3 size (N = 128): one sector's backprojection of a full-range
+    random int32 cotangent (4.3 GB, sums wrap), element by element against
+    the oracle's reversed Algorithm 3."""
+    N = 128
+    r = synth.raw_int32((1, N, N, 2 * N, 2 * N), 740 + k)
+    got = drt.lines_adjoint(torch.from_numpy(r).cuda(), [k]).cpu().numpy()
+    torch.cuda.empty_cache()
+    np.testing.assert_array_equal(got, oracle_mod.lines_adjoint(r, [k]))
 
 
 def test_lines_adjoint_dot_product_n128(drt):

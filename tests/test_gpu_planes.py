@@ -12,6 +12,8 @@ import torch
 
 import synth
 
+from _paper_refs import lline_rec
+
 pytestmark = pytest.mark.gpu
 
 FTOL = 1e-5
@@ -62,9 +64,9 @@ def test_forward_mid_sizes_exact(drt, oracle_mod, N):
 
 
 def test_config_c2_full_size(drt, oracle_mod):
-    """N = 256 uint8 sparse volume with embedded planes: two dodecants in full
-    against Algorithm 1, 10^5 random cells against the definition over all
-    twelve, and the mass invariant on every slope pair."""
+    """N = 256 uint8 sparse volume with embedded planes: all twelve dodecants
+    in full against Algorithm 1, 10^5 random cells against the definition,
+    and the mass invariant on every slope pair."""
     N = 256
     f = synth.c2_volume(N)
     R = drt.planes_forward(torch.from_numpy(f).cuda())
@@ -72,10 +74,11 @@ def test_config_c2_full_size(drt, oracle_mod):
     mass = R.to(torch.int64).sum(dim=3)
     assert bool((mass == total).all())
     assert bool((R[:, :, :, :2] == 0).all())
-    for k in (0, 5):
-        np.testing.assert_array_equal(R[k].cpu().numpy(), oracle_mod.planes_forward(f, [k])[0])
-    rng = np.random.default_rng(123)
     Rc = R.cpu().numpy()
+    del R
+    for k in range(12):
+        np.testing.assert_array_equal(Rc[k], oracle_mod.planes_forward(f, [k])[0], err_msg=f"dodecant {k}")
+    rng = np.random.default_rng(123)
     per = 100_000 // 12 + 1
     for k in range(12):
         g = oracle_mod.dodecant_volume(f.astype(np.int32), k)
@@ -84,6 +87,73 @@ def test_config_c2_full_size(drt, oracle_mod):
         d = rng.integers(0, 3 * N, per)
         for a, b, c in zip(s1, s2, d):
             assert oracle_mod.planes_cell(g, int(a), int(b), int(c)) == int(Rc[k, a, b, c])
+
+
+def _digital_plane(oracle_mod, N, k, s1, s2, dp):
+    """Flat indices into f[x][y][z] of the voxels of the digital plane
+    z' = l_{s1}(x') + l_{s2}(y') + dp of dodecant k's frame (eq.(3DfDRT)),
+    with the digital line in its recursive form (an independent restatement)
+    and the frame map of Algorithm 2 as the oracle reads it."""
+    n = N.bit_length() - 1
+    l1 = np.array([lline_rec(n, s1, u) for u in range(N)], dtype=np.int64)
+    l2 = np.array([lline_rec(n, s2, u) for u in range(N)], dtype=np.int64)
+    z = l1[:, None] + l2[None, :] + dp
+    ok = (z >= 0) & (z < N)
+    x, y = np.nonzero(ok)
+    return oracle_mod.dodecant_src_index(N, k)[x, y, z[ok]]
+
+
+def _random_planes(rng, N, count):
+    out = []
+    for _ in range(count):
+        k = int(rng.integers(0, 12))
+        s1, s2 = int(rng.integers(0, N)), int(rng.integers(0, N))
+        dp = int(rng.integers(-(s1 + s2), N))  # the plane meets the cube
+        out.append((k, s1, s2, dp))
+    return out
+
+
+def test_config_c2_embedded_planes(drt, oracle_mod):
+    """Config 2 with 8 digital planes of eq.(3DfDRT) set to 255 in random
+    dodecant frames: each plane's own cell R[k][s1][s2][dp + 2N] is 255 times
+    its voxel count (every voxel on it is 255)."""
+    N = 256
+    f = synth.c2_volume(N)
+    rng = np.random.default_rng(2024)
+    planes = _random_planes(rng, N, 8)
+    flat = f.reshape(-1)
+    voxels = []
+    for k, s1, s2, dp in planes:
+        idx = _digital_plane(oracle_mod, N, k, s1, s2, dp)
+        assert idx.size > 0
+        flat[idx] = 255
+        voxels.append(idx)
+    R = drt.planes_forward(torch.from_numpy(f).cuda())
+    for (k, s1, s2, dp), idx in zip(planes, voxels):
+        assert int(R[k, s1, s2, dp + 2 * N]) == 255 * idx.size, (k, s1, s2, dp)
+
+
+@pytest.mark.parametrize("N", [32, 64])
+def test_embedded_planes_over_dense_background(drt, oracle_mod, N):
+    """Digital planes added (value 1000 per plane through a voxel) to a dense
+    int32 background: each plane's cell equals 1000 times the number of
+    (plane, voxel) incidences on it plus the brute-force sum of the
+    background voxels on it (the definition, cell by cell)."""
+    bg = synth.random_int32((N, N, N), 900 + N, 0, 256)
+    rng = np.random.default_rng(910 + N)
+    planes = _random_planes(rng, N, 12)
+    cnt = np.zeros(N ** 3, dtype=np.int64)
+    voxels = []
+    for p in planes:
+        idx = _digital_plane(oracle_mod, N, *p)
+        cnt[idx] += 1
+        voxels.append(idx)
+    f = (bg.reshape(-1) + 1000 * cnt).astype(np.int32).reshape(N, N, N)
+    R = drt.planes_forward(torch.from_numpy(f).cuda()).cpu().numpy()
+    for (k, s1, s2, dp), idx in zip(planes, voxels):
+        g = oracle_mod.dodecant_volume(bg, k)
+        want = 1000 * int(cnt[idx].sum()) + oracle_mod.planes_cell(g, s1, s2, dp + 2 * N)
+        assert int(R[k, s1, s2, dp + 2 * N]) == want, (k, s1, s2, dp)
 
 
 @pytest.mark.parametrize("N", [4, 16, 64])
@@ -190,3 +260,21 @@ def test_planes_global_layout_n256_matches_dodecant_outputs(drt, oracle_mod):
     G = drt.planes_forward_global(vol).cpu().numpy()
     R = drt.planes_forward(vol).cpu().numpy()
     np.testing.assert_array_equal(G, oracle_mod.place_global(R))
+
+
+@pytest.mark.skipif(not torch.cuda.is_available() or torch.cuda.device_count() < 2,
+                    reason="needs a second GPU to make another device current")
+def test_calls_on_another_device_are_rejected(drt):
+    """A plan belongs to the device current at its creation: a forward call
+    made with another device current is an argument error and enqueues
+    nothing (its status word lives on the plan's device)."""
+    import ctypes
+
+    N = 8
+    plan = drt.get_plan(N, torch.int32)
+    f = torch.zeros((N, N, N), dtype=torch.int32, device="cuda:0")
+    out = torch.zeros((12, N, N, 3 * N), dtype=torch.int32, device="cuda:0")
+    lib = drt._abi.lib()
+    with torch.cuda.device(1):
+        rc = lib.drt3d_planes_forward(plan.handle, f.data_ptr(), out.data_ptr(), 0xFFF, None, 0, None)
+    assert rc == 1  # DRT3D_ERR_INVALID_ARG

@@ -50,11 +50,9 @@ def test_noalloc_matches_the_workspace_entry_point_on_two_calls(drt, N, dtype, m
         got = torch.full_like(want, 7)
         assert _noalloc(drt, plan, f, got, mask) == 0
         torch.cuda.synchronize()
-        if dtype == torch.float32:
-            # same kernels on the same data: identical up to the float tolerance used elsewhere
-            assert torch.allclose(got, want, rtol=1e-5, atol=1e-5)
-        else:
-            assert torch.equal(got, want), f"call {call}"
+        # same kernels on the same data: identical bit for bit, float32 included
+        # (a stale or aliased scratch value would show as any difference)
+        assert torch.equal(got, want), f"call {call}"
 
 
 def test_noalloc_rejects_calls_beyond_its_scratch(drt):
