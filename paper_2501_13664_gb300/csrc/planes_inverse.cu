@@ -417,6 +417,305 @@ planes_inv_pass(const __grid_constant__ InvLaunch L) {
     if (__any_sync(0xffffffffu, bad) && lane == 0) flag(L.status, DRT3D_ERR_NOT_IN_RANGE);
 }
 
+// ---------------------------------------------------------------------------
+// Aligned-row variant (rows of at most 896 displacements, i.e. N <= 256).
+//
+// Same stage algebra as above, but every row is kept physically aligned in
+// shared memory: element i of a slot is displacement base + i.  The shift of
+// hi (hi[i] = nT[i - S]) is applied once, when hi is written: lane l holds
+// nT over its chunk [l CH, l CH + CH) and writes the aligned block
+// [l CH + sa, l CH + sa + CH), sa = S & ~3, whose first r = S & 3 elements
+// are the last r of lane l - 1's chunk (one shuffle each); below the
+// stored window T is constant (Delta vanishes there), so hi[i] for i < S is
+// nT[0] while base + i - S >= 0 and 0 below displacement 0.  Every later
+// access is then an aligned 16-byte vector at the lane's own chunk.  CH is
+// 4 VPL with VPL odd, so the 8 lanes of each quarter-warp phase of an LDS.128
+// or STS.128 at a stride of CH words touch 8 distinct bank groups.
+//
+// The slots hold 32 CH words (the lanes' chunks) plus room for the shifted
+// block of the last lane.  Positions in [W, 32 CH) are zero at load; lo stays
+// zero there and hi is zero there whenever the pair passes the range check
+// (nT must vanish above W - 1 - S), so they never disturb the suffix sums of
+// data in the range of the forward map.
+template <int CH>
+__device__ __forceinline__ void load_chunk(const uint32_t* s, int c0, uint32_t (&v)[CH]) {
+#pragma unroll
+    for (int k = 0; k < CH / 4; ++k) {
+        const uint4 w = lds4(s, c0 + 4 * k);
+        v[4 * k] = w.x; v[4 * k + 1] = w.y; v[4 * k + 2] = w.z; v[4 * k + 3] = w.w;
+    }
+}
+
+template <int CH>
+__device__ __forceinline__ void store_chunk(uint32_t* s, int c0, const uint32_t (&v)[CH]) {
+#pragma unroll
+    for (int k = 0; k < CH / 4; ++k) sts4(s, c0 + 4 * k, make_uint4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
+}
+
+// hi over the lane's aligned block at c0 + sa: element j is nT[c0 + j - RR]
+// (j >= RR, this lane) or the previous lane's nT[c0 - RR + j] (j < RR); for
+// lane 0 those positions lie below S and take `fill(i)`.
+template <int CH, int RR>
+__device__ __forceinline__ void store_shifted(uint32_t* s, int c0, int sa, const uint32_t (&x)[CH], int lane,
+                                              uint32_t nt0, int fill_from) {
+    uint32_t e[CH];
+#pragma unroll
+    for (int j = 0; j < RR; ++j) {
+        const uint32_t p = __shfl_up_sync(0xffffffffu, x[CH - RR + j], 1);
+        // lane 0: position sa + j < S, below the stored window's shifted copy
+        e[j] = lane > 0 ? p : (sa + j >= fill_from ? nt0 : 0u);
+    }
+#pragma unroll
+    for (int j = RR; j < CH; ++j) e[j] = x[j - RR];
+    store_chunk<CH>(s, c0 + sa, e);
+}
+
+template <int G, int VPL>
+__global__ void __launch_bounds__(inv_warps(G) * 32, (G >= 4 ? (VPL >= 7 ? 3 : 4) : (VPL >= 7 ? 5 : 8)))
+planes_inv_group(const __grid_constant__ InvLaunch L) {
+    constexpr int R = 1 << G;
+    constexpr int NW = inv_warps(G);
+    constexpr int CH = 4 * VPL;
+    constexpr int RUN = VPL;  // suffix-sum run length (4 runs per chunk)
+    extern __shared__ __align__(16) uint32_t rows_al[];
+    __shared__ int slot[R];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int N = L.N, m0 = L.m0;
+    const int base = L.gin.base;
+    const int W = L.dmax - base;  // stored row length (a multiple of 4, at most 32 CH)
+    const int RS = 32 * CH + (((1 << (m0 + G - 1)) + 3) & ~3);  // slot words
+    unsigned unit = blockIdx.x;
+    const int sg = (int)(unit & ((1u << m0) - 1)); unit >>= m0;
+    const int wb = L.n - m0 - G;
+    const int wq = (int)(unit & ((1u << wb) - 1));
+    const int j = (int)(unit >> wb);
+    const long long rs_axis = L.axis == 0 ? N : 1;
+    const long long rs_other = L.axis == 0 ? 1 : N;
+    const int c0 = lane * CH;
+
+    // ---- load the unit's rows o(t) into slots t, zeros past W
+    {
+        const uint32_t* in = static_cast<const uint32_t*>(L.in);
+#pragma unroll 1
+        for (int t = warp; t < R; t += NW) {
+            const long long row = (long long)(t + (sg << G) + (wq << (m0 + G))) * rs_axis + (long long)j * rs_other;
+            const uint32_t* src = in + row * L.gin.pitch;
+            uint4 w[VPL];
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) {
+                const int i = 4 * (lane + 32 * v);
+                w[v] = i < W ? __ldg(reinterpret_cast<const uint4*>(src + i)) : make_uint4(0u, 0u, 0u, 0u);
+            }
+            uint32_t* dst = rows_al + t * RS;
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) sts4(dst, 4 * (lane + 32 * v), w[v]);
+        }
+    }
+    if (threadIdx.x < R) slot[threadIdx.x] = threadIdx.x;
+    __syncthreads();
+
+#pragma unroll 1
+    for (int J = G - 1; J >= 0; --J) {
+        const int half = 1 << J;
+        {
+            const int p = warp;  // one pair per warp
+            const int q = p >> J, tau = p & (half - 1);
+            const int r0 = 2 * tau + (q << (J + 1));
+            const int S = (sg << J) + tau;  // slope so far at global stage m0 + J
+            uint32_t* s0 = rows_al + slot[r0] * RS;
+            uint32_t* s1 = rows_al + slot[r0 + 1] * RS;
+            uint32_t a[CH], x[CH];
+            load_chunk<CH>(s0, c0, a);
+            load_chunk<CH>(s1, c0, x);
+#pragma unroll
+            for (int k = 0; k < CH; ++k) x[k] = a[k] - x[k];  // out_0 - out_1 = -Delta
+            // chunk suffix sums as 4 independent runs, then the runs' carries
+#pragma unroll
+            for (int k = RUN - 2; k >= 0; --k)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) x[RUN * b + k] += x[RUN * b + k + 1];
+            uint32_t rc[4];
+            rc[3] = 0u;
+            rc[2] = x[3 * RUN];
+            rc[1] = rc[2] + x[2 * RUN];
+            rc[0] = rc[1] + x[RUN];
+            const uint32_t tot = x[0] + rc[0];
+            uint32_t y = tot;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t z = __shfl_down_sync(0xffffffffu, y, off);
+                if (lane + off < 32) y += z;
+            }
+            const uint32_t carry = y - tot;  // chunks above this lane's
+#pragma unroll
+            for (int b = 0; b < 4; ++b) rc[b] += carry;
+#pragma unroll
+            for (int k = 0; k < CH; ++k) {
+                x[k] += rc[k / RUN];  // nT = -T
+                a[k] -= x[k];         // lo = out_0 + T
+            }
+            // Data in the range has T = 0 above W - 1 - S.
+            bool bad = false;
+            if (c0 + CH > W - S) {
+#pragma unroll
+                for (int k = 0; k < CH; ++k) bad |= (c0 + k >= W - S) && x[k] != 0u;
+            }
+            if (__any_sync(0xffffffffu, bad) && lane == 0) flag(L.status, DRT3D_ERR_NOT_IN_RANGE);
+            const uint32_t nt0 = __shfl_sync(0xffffffffu, x[0], 0);
+            __syncwarp();  // both rows read by every lane before any lane writes
+            store_chunk<CH>(s0, c0, a);
+            const int r = S & 3, sa = S - r;
+            const int fill_from = S - base;  // hi[i] = nT[0] for S - base <= i < S, 0 below
+            switch (r) {
+            case 0: store_shifted<CH, 0>(s1, c0, sa, x, lane, nt0, fill_from); break;
+            case 1: store_shifted<CH, 1>(s1, c0, sa, x, lane, nt0, fill_from); break;
+            case 2: store_shifted<CH, 2>(s1, c0, sa, x, lane, nt0, fill_from); break;
+            default: store_shifted<CH, 3>(s1, c0, sa, x, lane, nt0, fill_from); break;
+            }
+            // positions [0, sa) of hi lie below S: nT[0], or 0 below displacement 0
+            for (int v = lane; 4 * v < sa; v += 32) {
+                uint32_t e[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) e[k] = 4 * v + k >= fill_from ? nt0 : 0u;
+                sts4(s1, 4 * v, make_uint4(e[0], e[1], e[2], e[3]));
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            // new slot of every row of stage J (lane r): lo stays in out_0's
+            // slot, hi in out_1's
+            const int r = threadIdx.x;
+            int ns = 0;
+            if (r < R) {
+                const int hb = (r >> J) & 1;
+                const int a = r - (hb << J);
+                const int q = a >> (J + 1), tau = a & (half - 1);
+                ns = slot[2 * tau + (q << (J + 1)) + hb];
+            }
+            __syncwarp();
+            if (r < R) slot[r] = ns;
+        }
+        __syncthreads();
+    }
+
+    // ---- store the unit's input rows a(u) = sg + (u << m0) + (w << (m0 + G));
+    // recovered values below the output geometry's lower bound must vanish.
+    bool bad = false;
+    if (!L.scatter) {
+        const int lo_out = L.lo_out;
+        const int dlt = L.gout.base - base;  // >= 0, a multiple of 4
+        uint32_t* out = static_cast<uint32_t*>(L.out);
+#pragma unroll 1
+        for (int u = warp; u < R; u += NW) {
+            const int a = sg + (u << m0) + (wq << (m0 + G));
+            const long long row = (long long)a * rs_axis + (long long)j * rs_other;
+            uint32_t* dst = out + row * L.gout.pitch - dlt;  // element i of the stored row
+            const uint32_t* srow = rows_al + slot[u] * RS;
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) {
+                const int i = 4 * (lane + 32 * v);
+                if (i >= W) break;
+                const uint4 w = lds4(srow, i);
+                const int d = base + i;
+                if (d < lo_out) {
+                    bad |= (d < lo_out && w.x != 0u) || (d + 1 < lo_out && w.y != 0u) ||
+                           (d + 2 < lo_out && w.z != 0u) || (d + 3 < lo_out && w.w != 0u);
+                }
+                if (i >= dlt) *reinterpret_cast<uint4*>(dst + i) = w;
+            }
+        }
+    } else {
+        // Stage-0 rows: the volume sits at d in [2N, 3N) of frame row (x', y').
+        int32_t* vol = static_cast<int32_t*>(L.out);
+        const Affine& M = L.map;
+        const long long s_row = L.axis == 0 ? M.sx : M.sy;  // volume stride between rows u, u + 1
+        if (M.sz == 1 || (s_row != 1 && s_row != -1)) {
+#pragma unroll 1
+            for (int u = warp; u < R; u += NW) {
+                const int a = sg + (u << m0) + (wq << (m0 + G));
+                const int xp = L.axis == 0 ? a : j, yp = L.axis == 0 ? j : a;
+                const long long rb = M.o0 + xp * M.sx + yp * M.sy;
+                const uint32_t* srow = rows_al + slot[u] * RS;
+                for (int i = 4 * lane; i < W; i += 128) {
+                    const uint4 w = lds4(srow, i);
+                    const uint32_t e[4] = {w.x, w.y, w.z, w.w};
+                    const int d = base + i;
+                    if (M.sz == 1 && d >= 2 * N && ((rb + d - 2 * N) & 3) == 0) {
+                        *reinterpret_cast<uint4*>(vol + rb + (d - 2 * N)) = w;
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            if (d + k < 2 * N) bad |= e[k] != 0u;
+                            else vol[rb + (long long)(d + k - 2 * N) * M.sz] = (int32_t)e[k];
+                        }
+                    }
+                }
+            }
+        } else {
+            // lanes along the rows u (unit stride in the volume)
+            constexpr int NT = NW * 32;
+            for (int idx = threadIdx.x; idx < R * W; idx += NT) {
+                const int i = idx / R, u = idx - i * R;
+                const int d = base + i;
+                const uint32_t e = rows_al[slot[u] * RS + i];
+                if (d < 2 * N) {
+                    bad |= e != 0u;
+                } else {
+                    const int a = sg + (u << m0) + (wq << (m0 + G));
+                    const int xp = L.axis == 0 ? a : j, yp = L.axis == 0 ? j : a;
+                    vol[M.o0 + xp * M.sx + yp * M.sy + (long long)(d - 2 * N) * M.sz] = (int32_t)e;
+                }
+            }
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) flag(L.status, DRT3D_ERR_NOT_IN_RANGE);
+}
+
+// Chunk vectors per lane of the aligned-row kernel for rows of W displacements
+// (0 when the rows are too long or not made of whole 16-byte vectors).
+int inv_group_vpl(int W, const InvLaunch& L) {
+    if (W % 4 != 0 || L.gin.pitch % 4 != 0 || (!L.scatter && (L.gout.pitch % 4 != 0 || L.gout.base % 4 != 0)))
+        return 0;
+    for (int vpl : {1, 3, 5, 7})
+        if (W <= 128 * vpl) return vpl;
+    return 0;
+}
+
+size_t inv_group_smem(int G, int m0, int vpl) {
+    return (size_t)(1 << G) * (32 * 4 * vpl + (((1 << (m0 + G - 1)) + 3) & ~3)) * 4;
+}
+
+template <int G, int VPL>
+cudaError_t launch_inv_group(const InvLaunch& L, cudaStream_t s) {
+    const size_t smem = inv_group_smem(G, L.m0, VPL);
+    auto kern = planes_inv_group<G, VPL>;
+    static DeviceOnce attr_done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (!attr_done.done(dev)) {
+        // the largest slot set this instantiation can need (m0 + G <= 10)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)inv_group_smem(G, 10 - G, VPL));
+        if (e != cudaSuccess) return e;
+        attr_done.mark(dev);
+    }
+    const unsigned units = (unsigned)((long long)L.N << (L.n - G));
+    kern<<<units, inv_warps(G) * 32, smem, s>>>(L);
+    return cudaGetLastError();
+}
+
+template <int G>
+cudaError_t launch_inv_group_g(const InvLaunch& L, int vpl, cudaStream_t s) {
+    switch (vpl) {
+    case 1: return launch_inv_group<G, 1>(L, s);
+    case 3: return launch_inv_group<G, 3>(L, s);
+    case 5: return launch_inv_group<G, 5>(L, s);
+    default: return launch_inv_group<G, 7>(L, s);
+    }
+}
+
 size_t inv_smem(int G, int W, int m0) {
     return (size_t)(1 << G) * inv_slot_words(W, m0, G, inv_chunk_width(W)) * 4;
 }
@@ -471,6 +770,16 @@ cudaError_t launch_inv_g(const InvLaunch& L, cudaStream_t s) {
 size_t inverse_smem_bytes(int N, int G, int base, int m0) { return inv_smem(G, 3 * N - base, m0); }
 
 cudaError_t launch_planes_inverse_pass(const InvLaunch& L, int G, cudaStream_t s) {
+    const int vpl = inv_group_vpl(L.dmax - L.gin.base, L);
+    if (vpl > 0) {
+        switch (G) {
+        case 1: return launch_inv_group_g<1>(L, vpl, s);
+        case 2: return launch_inv_group_g<2>(L, vpl, s);
+        case 3: return launch_inv_group_g<3>(L, vpl, s);
+        case 4: return launch_inv_group_g<4>(L, vpl, s);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (G) {
     case 1: return launch_inv_g<1>(L, s);
     case 2: return launch_inv_g<2>(L, s);
