@@ -40,6 +40,7 @@
 // take part in the shuffle scans only: they read the last chunk's addresses
 // (served by broadcast, no extra traffic) and store nothing.
 #include "internal.cuh"
+#include "tma.cuh"
 
 namespace drt3d {
 namespace {
@@ -454,20 +455,49 @@ __device__ __forceinline__ void store_chunk(uint32_t* s, int c0, const uint32_t 
 
 // hi over the lane's aligned block at c0 + sa: element j is nT[c0 + j - RR]
 // (j >= RR, this lane) or the previous lane's nT[c0 - RR + j] (j < RR); for
-// lane 0 those positions lie below S and take `fill(i)`.
+// lane 0 those positions lie below S and take the fill value (nT[0] from
+// position fill_from on, 0 below).
 template <int CH, int RR>
-__device__ __forceinline__ void store_shifted(uint32_t* s, int c0, int sa, const uint32_t (&x)[CH], int lane,
-                                              uint32_t nt0, int fill_from) {
-    uint32_t e[CH];
+__device__ __forceinline__ void realign(const uint32_t (&x)[CH], int lane, int sa, uint32_t nt0, int fill_from,
+                                        uint32_t (&e)[CH]) {
 #pragma unroll
     for (int j = 0; j < RR; ++j) {
         const uint32_t p = __shfl_up_sync(0xffffffffu, x[CH - RR + j], 1);
-        // lane 0: position sa + j < S, below the stored window's shifted copy
         e[j] = lane > 0 ? p : (sa + j >= fill_from ? nt0 : 0u);
     }
 #pragma unroll
     for (int j = RR; j < CH; ++j) e[j] = x[j - RR];
-    store_chunk<CH>(s, c0 + sa, e);
+}
+
+template <int CH>
+__device__ __forceinline__ void realign_any(int r, const uint32_t (&x)[CH], int lane, int sa, uint32_t nt0,
+                                            int fill_from, uint32_t (&e)[CH]) {
+    switch (r) {
+    case 0: realign<CH, 0>(x, lane, sa, nt0, fill_from, e); break;
+    case 1: realign<CH, 1>(x, lane, sa, nt0, fill_from, e); break;
+    case 2: realign<CH, 2>(x, lane, sa, nt0, fill_from, e); break;
+    default: realign<CH, 3>(x, lane, sa, nt0, fill_from, e); break;
+    }
+}
+
+// Upper bound (ns) on the wait for a bulk row copy: a copy that has not
+// landed by then is reported as a time-out.
+constexpr unsigned long long kBulkWaitNs = 200000000ull;
+
+// Physical slot of logical row r once stages G-1 .. J1 have been undone.
+// Undoing stage J keeps lo in out_0's slot and hi in out_1's: the row with
+// position bit J = hb and low bits tau came from stage-(J+1) row
+// 2 tau + hb of its block, i.e. the low J + 1 bits rotated left by one.
+template <int G>
+__device__ __forceinline__ int phys_slot(int r, int J1) {
+#pragma unroll
+    for (int J = 0; J < G; ++J) {
+        if (J >= J1) {
+            const int m = (2 << J) - 1;
+            r = (r & ~m) | (((r << 1) | ((r >> J) & 1)) & m);
+        }
+    }
+    return r;
 }
 
 template <int G, int VPL>
@@ -476,15 +506,16 @@ planes_inv_group(const __grid_constant__ InvLaunch L) {
     constexpr int R = 1 << G;
     constexpr int NW = inv_warps(G);
     constexpr int CH = 4 * VPL;
+    constexpr int SPAN = 32 * CH;
     constexpr int RUN = VPL;  // suffix-sum run length (4 runs per chunk)
     extern __shared__ __align__(16) uint32_t rows_al[];
-    __shared__ int slot[R];
+    __shared__ __align__(8) uint64_t bar[NW];  // one per warp: its pair's two input rows
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = L.N, m0 = L.m0;
     const int base = L.gin.base;
-    const int W = L.dmax - base;  // stored row length (a multiple of 4, at most 32 CH)
-    const int RS = 32 * CH + (((1 << (m0 + G - 1)) + 3) & ~3);  // slot words
+    const int W = L.dmax - base;  // stored row length (a multiple of 4, at most SPAN)
+    const int RS = SPAN + (((1 << (m0 + G - 1)) + 3) & ~3);  // slot words
     unsigned unit = blockIdx.x;
     const int sg = (int)(unit & ((1u << m0) - 1)); unit >>= m0;
     const int wb = L.n - m0 - G;
@@ -493,163 +524,158 @@ planes_inv_group(const __grid_constant__ InvLaunch L) {
     const long long rs_axis = L.axis == 0 ? N : 1;
     const long long rs_other = L.axis == 0 ? 1 : N;
     const int c0 = lane * CH;
+    const Affine& M = L.map;
+    // Final rows leave by bulk copies: buffer rows, or volume rows whose z'
+    // runs forward in memory from a 16-byte-aligned start.
+    const bool direct = !L.scatter || (M.sz == 1 && ((M.o0 | M.sx | M.sy) & 3) == 0);
+    // Positions below LO must vanish after the group; only [dlt, W) is stored.
+    const int LO = L.scatter ? 2 * N - base : L.lo_out - base;
+    const int dlt = L.scatter ? 2 * N - base : L.gout.base - base;
+    bool bad = false;
 
-    // ---- load the unit's rows o(t) into slots t, zeros past W
+    // ---- the warp's pair of the group's first stage: input rows o(2p),
+    // o(2p + 1) into slots 2p, 2p + 1 by two bulk copies; zeros past W.
     {
-        const uint32_t* in = static_cast<const uint32_t*>(L.in);
-#pragma unroll 1
-        for (int t = warp; t < R; t += NW) {
-            const long long row = (long long)(t + (sg << G) + (wq << (m0 + G))) * rs_axis + (long long)j * rs_other;
-            const uint32_t* src = in + row * L.gin.pitch;
-            uint4 w[VPL];
-#pragma unroll
-            for (int v = 0; v < VPL; ++v) {
-                const int i = 4 * (lane + 32 * v);
-                w[v] = i < W ? __ldg(reinterpret_cast<const uint4*>(src + i)) : make_uint4(0u, 0u, 0u, 0u);
-            }
-            uint32_t* dst = rows_al + t * RS;
-#pragma unroll
-            for (int v = 0; v < VPL; ++v) sts4(dst, 4 * (lane + 32 * v), w[v]);
+        const int p = warp;
+        uint32_t* s0 = rows_al + (2 * p) * RS;
+        uint32_t* s1 = s0 + RS;
+        if (lane == 0) {
+            tma::mbar_init(&bar[p], 1);
+            tma::fence_barrier_init();
+            const uint32_t* in = static_cast<const uint32_t*>(L.in);
+            const long long orow = (long long)(2 * p + (sg << G) + (wq << (m0 + G))) * rs_axis + (long long)j * rs_other;
+            const uint32_t* g0 = in + orow * L.gin.pitch;
+            tma::mbar_arrive_expect_tx(&bar[p], 2u * W * 4u);
+            tma::bulk_load(s0, g0, W * 4u, &bar[p]);
+            tma::bulk_load(s1, g0 + rs_axis * L.gin.pitch, W * 4u, &bar[p]);
+        }
+        for (int i = W + 4 * lane; i < SPAN; i += 128) {
+            sts4(s0, i, make_uint4(0u, 0u, 0u, 0u));
+            sts4(s1, i, make_uint4(0u, 0u, 0u, 0u));
+        }
+        __syncwarp();
+        if (!tma::mbar_wait(&bar[p], 0, kBulkWaitNs)) {
+            if (lane == 0) flag(L.status, DRT3D_ERR_TIMEOUT);
+            tma::mbar_wait(&bar[p], 0, kBulkWaitNs);  // once more for the copies in flight
         }
     }
-    if (threadIdx.x < R) slot[threadIdx.x] = threadIdx.x;
-    __syncthreads();
 
 #pragma unroll 1
     for (int J = G - 1; J >= 0; --J) {
         const int half = 1 << J;
+        const int p = warp;  // one pair per warp
+        const int q = p >> J, tau = p & (half - 1);
+        const int r0 = 2 * tau + (q << (J + 1));
+        const int S = (sg << J) + tau;  // slope so far at global stage m0 + J
+        uint32_t a[CH], x[CH];
+        uint32_t* s0 = rows_al + phys_slot<G>(r0, J + 1) * RS;
+        uint32_t* s1 = rows_al + phys_slot<G>(r0 + 1, J + 1) * RS;
+        load_chunk<CH>(s0, c0, a);
+        load_chunk<CH>(s1, c0, x);
+        // data in the range has Delta = 0 above W - 1 - S
         {
-            const int p = warp;  // one pair per warp
-            const int q = p >> J, tau = p & (half - 1);
-            const int r0 = 2 * tau + (q << (J + 1));
-            const int S = (sg << J) + tau;  // slope so far at global stage m0 + J
-            uint32_t* s0 = rows_al + slot[r0] * RS;
-            uint32_t* s1 = rows_al + slot[r0 + 1] * RS;
-            uint32_t a[CH], x[CH];
-            load_chunk<CH>(s0, c0, a);
-            load_chunk<CH>(s1, c0, x);
-#pragma unroll
-            for (int k = 0; k < CH; ++k) x[k] = a[k] - x[k];  // out_0 - out_1 = -Delta
-            // chunk suffix sums as 4 independent runs, then the runs' carries
-#pragma unroll
-            for (int k = RUN - 2; k >= 0; --k)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) x[RUN * b + k] += x[RUN * b + k + 1];
-            uint32_t rc[4];
-            rc[3] = 0u;
-            rc[2] = x[3 * RUN];
-            rc[1] = rc[2] + x[2 * RUN];
-            rc[0] = rc[1] + x[RUN];
-            const uint32_t tot = x[0] + rc[0];
-            uint32_t y = tot;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t z = __shfl_down_sync(0xffffffffu, y, off);
-                if (lane + off < 32) y += z;
-            }
-            const uint32_t carry = y - tot;  // chunks above this lane's
-#pragma unroll
-            for (int b = 0; b < 4; ++b) rc[b] += carry;
-#pragma unroll
-            for (int k = 0; k < CH; ++k) {
-                x[k] += rc[k / RUN];  // nT = -T
-                a[k] -= x[k];         // lo = out_0 + T
-            }
-            // Data in the range has T = 0 above W - 1 - S.
-            bool bad = false;
-            if (c0 + CH > W - S) {
-#pragma unroll
-                for (int k = 0; k < CH; ++k) bad |= (c0 + k >= W - S) && x[k] != 0u;
-            }
-            if (__any_sync(0xffffffffu, bad) && lane == 0) flag(L.status, DRT3D_ERR_NOT_IN_RANGE);
-            const uint32_t nt0 = __shfl_sync(0xffffffffu, x[0], 0);
-            __syncwarp();  // both rows read by every lane before any lane writes
-            store_chunk<CH>(s0, c0, a);
-            const int r = S & 3, sa = S - r;
-            const int fill_from = S - base;  // hi[i] = nT[0] for S - base <= i < S, 0 below
-            switch (r) {
-            case 0: store_shifted<CH, 0>(s1, c0, sa, x, lane, nt0, fill_from); break;
-            case 1: store_shifted<CH, 1>(s1, c0, sa, x, lane, nt0, fill_from); break;
-            case 2: store_shifted<CH, 2>(s1, c0, sa, x, lane, nt0, fill_from); break;
-            default: store_shifted<CH, 3>(s1, c0, sa, x, lane, nt0, fill_from); break;
-            }
-            // positions [0, sa) of hi lie below S: nT[0], or 0 below displacement 0
-            for (int v = lane; 4 * v < sa; v += 32) {
-                uint32_t e[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) e[k] = 4 * v + k >= fill_from ? nt0 : 0u;
-                sts4(s1, 4 * v, make_uint4(e[0], e[1], e[2], e[3]));
-            }
+            bool top_bad = false;
+            for (int i = W - S + lane; i < W; i += 32) top_bad |= s0[i] != s1[i];
+            if (__any_sync(0xffffffffu, top_bad) && lane == 0) flag(L.status, DRT3D_ERR_NOT_IN_RANGE);
         }
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            // new slot of every row of stage J (lane r): lo stays in out_0's
-            // slot, hi in out_1's
-            const int r = threadIdx.x;
-            int ns = 0;
-            if (r < R) {
-                const int hb = (r >> J) & 1;
-                const int a = r - (hb << J);
-                const int q = a >> (J + 1), tau = a & (half - 1);
-                ns = slot[2 * tau + (q << (J + 1)) + hb];
-            }
+        __syncwarp();  // both rows read by every lane before any lane writes
+#pragma unroll
+        for (int k = 0; k < CH; ++k) x[k] = a[k] - x[k];  // out_0 - out_1 = -Delta
+        // chunk suffix sums as 4 independent runs, then the runs' carries
+#pragma unroll
+        for (int k = RUN - 2; k >= 0; --k)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) x[RUN * b + k] += x[RUN * b + k + 1];
+        uint32_t rc[4];
+        rc[3] = 0u;
+        rc[2] = x[3 * RUN];
+        rc[1] = rc[2] + x[2 * RUN];
+        rc[0] = rc[1] + x[RUN];
+        const uint32_t tot = x[0] + rc[0];
+        uint32_t y = tot;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t z = __shfl_down_sync(0xffffffffu, y, off);
+            if (lane + off < 32) y += z;
+        }
+        const uint32_t carry = y - tot;  // chunks above this lane's
+#pragma unroll
+        for (int b = 0; b < 4; ++b) rc[b] += carry;
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+            x[k] += rc[k / RUN];  // nT = -T
+            a[k] -= x[k];         // lo = out_0 + T
+        }
+        store_chunk<CH>(s0, c0, a);
+        const uint32_t nt0 = __shfl_sync(0xffffffffu, x[0], 0);
+        const int r = S & 3, sa = S - r;
+        const int fill_from = S - base;  // hi[i] = nT[0] for S - base <= i < S, 0 below
+        uint32_t e[CH];
+        realign_any<CH>(r, x, lane, sa, nt0, fill_from, e);  // hi over [c0 + sa, c0 + sa + CH)
+        store_chunk<CH>(s1, c0 + sa, e);
+        // positions [0, sa) of hi lie below S
+        for (int v = lane; 4 * v < sa; v += 32) {
+            uint32_t f[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) f[k] = 4 * v + k >= fill_from ? nt0 : 0u;
+            sts4(s1, 4 * v, make_uint4(f[0], f[1], f[2], f[3]));
+        }
+        if (J > 0 || !direct) {
+            __syncthreads();
+        } else {
+            // Stage 0 of the group: lo is input row a(2p), hi input row a(2p + 1).
+            // Values below LO must vanish; [dlt, W) of both rows leaves by two
+            // bulk copies once this warp's writes are visible to the async proxy.
             __syncwarp();
-            if (r < R) slot[r] = ns;
+            for (int i = 4 * lane; i < LO; i += 128) {
+                const uint4 u0 = lds4(s0, i), u1 = lds4(s1, i);
+                const uint32_t e0[4] = {u0.x | u1.x, u0.y | u1.y, u0.z | u1.z, u0.w | u1.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) bad |= i + k < LO && e0[k] != 0u;
+            }
+            tma::fence_proxy_async_shared();
+            __syncwarp();
+            if (lane == 0) {
+                const int ua = sg + ((2 * p) << m0) + (wq << (m0 + G));
+                const int ub = ua + (1 << m0);
+                uint32_t *da, *db;
+                if (!L.scatter) {
+                    uint32_t* out = static_cast<uint32_t*>(L.out);
+                    da = out + ((long long)ua * rs_axis + (long long)j * rs_other) * L.gout.pitch;
+                    db = out + ((long long)ub * rs_axis + (long long)j * rs_other) * L.gout.pitch;
+                } else {
+                    uint32_t* vol = static_cast<uint32_t*>(L.out);
+                    const long long ra = M.o0 + (L.axis == 0 ? (long long)ua * M.sx + (long long)j * M.sy
+                                                             : (long long)j * M.sx + (long long)ua * M.sy);
+                    da = vol + ra;
+                    db = vol + ra + (L.axis == 0 ? M.sx : M.sy) * (long long)(1 << m0);
+                }
+                tma::bulk_store(da, s0 + dlt, (W - dlt) * 4u);
+                tma::bulk_store(db, s1 + dlt, (W - dlt) * 4u);
+                tma::bulk_commit();
+                tma::bulk_wait_read();  // shared memory stays valid until the copies have read it
+            }
         }
-        __syncthreads();
     }
 
-    // ---- store the unit's input rows a(u) = sg + (u << m0) + (w << (m0 + G));
-    // recovered values below the output geometry's lower bound must vanish.
-    bool bad = false;
-    if (!L.scatter) {
-        const int lo_out = L.lo_out;
-        const int dlt = L.gout.base - base;  // >= 0, a multiple of 4
-        uint32_t* out = static_cast<uint32_t*>(L.out);
-#pragma unroll 1
-        for (int u = warp; u < R; u += NW) {
-            const int a = sg + (u << m0) + (wq << (m0 + G));
-            const long long row = (long long)a * rs_axis + (long long)j * rs_other;
-            uint32_t* dst = out + row * L.gout.pitch - dlt;  // element i of the stored row
-            const uint32_t* srow = rows_al + slot[u] * RS;
-#pragma unroll
-            for (int v = 0; v < VPL; ++v) {
-                const int i = 4 * (lane + 32 * v);
-                if (i >= W) break;
-                const uint4 w = lds4(srow, i);
-                const int d = base + i;
-                if (d < lo_out) {
-                    bad |= (d < lo_out && w.x != 0u) || (d + 1 < lo_out && w.y != 0u) ||
-                           (d + 2 < lo_out && w.z != 0u) || (d + 3 < lo_out && w.w != 0u);
-                }
-                if (i >= dlt) *reinterpret_cast<uint4*>(dst + i) = w;
-            }
-        }
-    } else {
-        // Stage-0 rows: the volume sits at d in [2N, 3N) of frame row (x', y').
+    if (!direct) {
+        // Volume rows not contiguous along z' (or reversed): from shared
+        // memory through the dodecant map.  Stage-0 rows hold the volume at d
+        // in [2N, 3N) of frame row (x', y').
         int32_t* vol = static_cast<int32_t*>(L.out);
-        const Affine& M = L.map;
         const long long s_row = L.axis == 0 ? M.sx : M.sy;  // volume stride between rows u, u + 1
-        if (M.sz == 1 || (s_row != 1 && s_row != -1)) {
+        if (s_row != 1 && s_row != -1) {
 #pragma unroll 1
             for (int u = warp; u < R; u += NW) {
                 const int a = sg + (u << m0) + (wq << (m0 + G));
                 const int xp = L.axis == 0 ? a : j, yp = L.axis == 0 ? j : a;
                 const long long rb = M.o0 + xp * M.sx + yp * M.sy;
-                const uint32_t* srow = rows_al + slot[u] * RS;
-                for (int i = 4 * lane; i < W; i += 128) {
-                    const uint4 w = lds4(srow, i);
-                    const uint32_t e[4] = {w.x, w.y, w.z, w.w};
+                const uint32_t* srow = rows_al + phys_slot<G>(u, 0) * RS;
+                for (int i = lane; i < W; i += 32) {
                     const int d = base + i;
-                    if (M.sz == 1 && d >= 2 * N && ((rb + d - 2 * N) & 3) == 0) {
-                        *reinterpret_cast<uint4*>(vol + rb + (d - 2 * N)) = w;
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            if (d + k < 2 * N) bad |= e[k] != 0u;
-                            else vol[rb + (long long)(d + k - 2 * N) * M.sz] = (int32_t)e[k];
-                        }
-                    }
+                    const uint32_t e = srow[i];
+                    if (d < 2 * N) bad |= e != 0u;
+                    else vol[rb + (long long)(d - 2 * N) * M.sz] = (int32_t)e;
                 }
             }
         } else {
@@ -658,7 +684,7 @@ planes_inv_group(const __grid_constant__ InvLaunch L) {
             for (int idx = threadIdx.x; idx < R * W; idx += NT) {
                 const int i = idx / R, u = idx - i * R;
                 const int d = base + i;
-                const uint32_t e = rows_al[slot[u] * RS + i];
+                const uint32_t e = rows_al[phys_slot<G>(u, 0) * RS + i];
                 if (d < 2 * N) {
                     bad |= e != 0u;
                 } else {
