@@ -488,16 +488,142 @@ constexpr unsigned long long kBulkWaitNs = 200000000ull;
 // Undoing stage J keeps lo in out_0's slot and hi in out_1's: the row with
 // position bit J = hb and low bits tau came from stage-(J+1) row
 // 2 tau + hb of its block, i.e. the low J + 1 bits rotated left by one.
-template <int G>
-__device__ __forceinline__ int phys_slot(int r, int J1) {
+template <int G, int J1>
+__device__ __forceinline__ int phys_slot(int r) {
 #pragma unroll
-    for (int J = 0; J < G; ++J) {
-        if (J >= J1) {
-            const int m = (2 << J) - 1;
-            r = (r & ~m) | (((r << 1) | ((r >> J) & 1)) & m);
-        }
+    for (int J = J1; J < G; ++J) {
+        constexpr int one = 1;
+        const int m = (2 * one << J) - 1;
+        r = (r & ~m) | (((r << 1) | ((r >> J) & 1)) & m);
     }
     return r;
+}
+
+// Per-CTA constants of the aligned-row kernel.
+struct InvCtx {
+    uint32_t* rows;  // slot 0
+    int RS, W, base, sg, wq, j, m0, c0, lane, warp, LO, dlt;
+    long long rs_axis, rs_other;
+    bool direct;
+};
+
+// Undo stage J of the group (one pair per warp), in place in the slots; the
+// group's last stage (J = 0) with `direct` sends both rows out by bulk copies.
+template <int G, int VPL, int J>
+__device__ __forceinline__ void inv_stage(const InvLaunch& L, const InvCtx& C, bool& bad) {
+    constexpr int CH = 4 * VPL;
+    constexpr int RUN = VPL;  // suffix-sum run length (4 runs per chunk)
+    constexpr int half = 1 << J;
+    const int lane = C.lane, c0 = C.c0, W = C.W;
+    const int p = C.warp;  // one pair per warp
+    const int q = p >> J, tau = p & (half - 1);
+    const int r0 = 2 * tau + (q << (J + 1));
+    const int S = (C.sg << J) + tau;  // slope so far at global stage m0 + J
+    uint32_t a[CH], x[CH];
+    uint32_t* s0 = C.rows + phys_slot<G, J + 1>(r0) * C.RS;
+    uint32_t* s1 = C.rows + phys_slot<G, J + 1>(r0 + 1) * C.RS;
+    load_chunk<CH>(s0, c0, a);
+    load_chunk<CH>(s1, c0, x);
+    // data in the range has Delta = 0 above W - 1 - S (S < 2^(m0 + J))
+    {
+        bool top_bad = false;
+        if (C.m0 + J <= 5) {
+            if (lane < S) top_bad = s0[W - S + lane] != s1[W - S + lane];
+        } else {
+            for (int i = W - S + lane; i < W; i += 32) top_bad |= s0[i] != s1[i];
+        }
+        if (__any_sync(0xffffffffu, top_bad) && lane == 0) flag(L.status, DRT3D_ERR_NOT_IN_RANGE);
+    }
+    __syncwarp();  // both rows read by every lane before any lane writes
+#pragma unroll
+    for (int k = 0; k < CH; ++k) x[k] = a[k] - x[k];  // out_0 - out_1 = -Delta
+    // chunk suffix sums as 4 independent runs, then the runs' carries
+#pragma unroll
+    for (int k = RUN - 2; k >= 0; --k)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) x[RUN * b + k] += x[RUN * b + k + 1];
+    uint32_t rc[4];
+    rc[3] = 0u;
+    rc[2] = x[3 * RUN];
+    rc[1] = rc[2] + x[2 * RUN];
+    rc[0] = rc[1] + x[RUN];
+    const uint32_t tot = x[0] + rc[0];
+    uint32_t y = tot;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t z = __shfl_down_sync(0xffffffffu, y, off);
+        if (lane + off < 32) y += z;
+    }
+    const uint32_t carry = y - tot;  // chunks above this lane's
+#pragma unroll
+    for (int b = 0; b < 4; ++b) rc[b] += carry;
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+        x[k] += rc[k / RUN];  // nT = -T
+        a[k] -= x[k];         // lo = out_0 + T
+    }
+    store_chunk<CH>(s0, c0, a);
+    const uint32_t nt0 = __shfl_sync(0xffffffffu, x[0], 0);
+    const int r = S & 3, sa = S - r;
+    const int fill_from = S - C.base;  // hi[i] = nT[0] for S - base <= i < S, 0 below
+    {
+        uint32_t e[CH];
+        realign_any<CH>(r, x, lane, sa, nt0, fill_from, e);  // hi over [c0 + sa, c0 + sa + CH)
+        store_chunk<CH>(s1, c0 + sa, e);
+    }
+    // positions [0, sa) of hi lie below S
+    if (4 * lane < sa) {
+        for (int v = lane; 4 * v < sa; v += 32) {
+            uint32_t f[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) f[k] = 4 * v + k >= fill_from ? nt0 : 0u;
+            sts4(s1, 4 * v, make_uint4(f[0], f[1], f[2], f[3]));
+        }
+    }
+    if (J > 0 || !C.direct) {
+        __syncthreads();
+        return;
+    }
+    // Stage 0 of the group: lo is input row a(2p), hi input row a(2p + 1).
+    // Values below LO must vanish; [dlt, W) of both rows leaves by two bulk
+    // copies once this warp's writes are visible to the async proxy.
+    __syncwarp();
+    for (int i = 4 * lane; i < C.LO; i += 128) {
+        const uint4 u0 = lds4(s0, i), u1 = lds4(s1, i);
+        const uint32_t e0[4] = {u0.x | u1.x, u0.y | u1.y, u0.z | u1.z, u0.w | u1.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) bad |= i + k < C.LO && e0[k] != 0u;
+    }
+    tma::fence_proxy_async_shared();
+    __syncwarp();
+    if (lane == 0) {
+        const int m0 = C.m0;
+        const int ua = C.sg + ((2 * p) << m0) + (C.wq << (m0 + G));
+        const int ub = ua + (1 << m0);
+        uint32_t *da, *db;
+        if (!L.scatter) {
+            uint32_t* out = static_cast<uint32_t*>(L.out);
+            da = out + ((long long)ua * C.rs_axis + (long long)C.j * C.rs_other) * L.gout.pitch;
+            db = out + ((long long)ub * C.rs_axis + (long long)C.j * C.rs_other) * L.gout.pitch;
+        } else {
+            const Affine& M = L.map;
+            uint32_t* vol = static_cast<uint32_t*>(L.out);
+            const long long ra = M.o0 + (L.axis == 0 ? (long long)ua * M.sx + (long long)C.j * M.sy
+                                                     : (long long)C.j * M.sx + (long long)ua * M.sy);
+            da = vol + ra;
+            db = vol + ra + (L.axis == 0 ? M.sx : M.sy) * (long long)(1 << m0);
+        }
+        tma::bulk_store(da, s0 + C.dlt, (W - C.dlt) * 4u);
+        tma::bulk_store(db, s1 + C.dlt, (W - C.dlt) * 4u);
+        tma::bulk_commit();
+        tma::bulk_wait_read();  // shared memory stays valid until the copies have read it
+    }
+}
+
+template <int G, int VPL, int J>
+__device__ __forceinline__ void inv_stages(const InvLaunch& L, const InvCtx& C, bool& bad) {
+    inv_stage<G, VPL, J>(L, C, bad);
+    if constexpr (J > 0) inv_stages<G, VPL, J - 1>(L, C, bad);
 }
 
 template <int G, int VPL>
@@ -560,102 +686,14 @@ planes_inv_group(const __grid_constant__ InvLaunch L) {
         }
     }
 
-#pragma unroll 1
-    for (int J = G - 1; J >= 0; --J) {
-        const int half = 1 << J;
-        const int p = warp;  // one pair per warp
-        const int q = p >> J, tau = p & (half - 1);
-        const int r0 = 2 * tau + (q << (J + 1));
-        const int S = (sg << J) + tau;  // slope so far at global stage m0 + J
-        uint32_t a[CH], x[CH];
-        uint32_t* s0 = rows_al + phys_slot<G>(r0, J + 1) * RS;
-        uint32_t* s1 = rows_al + phys_slot<G>(r0 + 1, J + 1) * RS;
-        load_chunk<CH>(s0, c0, a);
-        load_chunk<CH>(s1, c0, x);
-        // data in the range has Delta = 0 above W - 1 - S
-        {
-            bool top_bad = false;
-            for (int i = W - S + lane; i < W; i += 32) top_bad |= s0[i] != s1[i];
-            if (__any_sync(0xffffffffu, top_bad) && lane == 0) flag(L.status, DRT3D_ERR_NOT_IN_RANGE);
-        }
-        __syncwarp();  // both rows read by every lane before any lane writes
-#pragma unroll
-        for (int k = 0; k < CH; ++k) x[k] = a[k] - x[k];  // out_0 - out_1 = -Delta
-        // chunk suffix sums as 4 independent runs, then the runs' carries
-#pragma unroll
-        for (int k = RUN - 2; k >= 0; --k)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) x[RUN * b + k] += x[RUN * b + k + 1];
-        uint32_t rc[4];
-        rc[3] = 0u;
-        rc[2] = x[3 * RUN];
-        rc[1] = rc[2] + x[2 * RUN];
-        rc[0] = rc[1] + x[RUN];
-        const uint32_t tot = x[0] + rc[0];
-        uint32_t y = tot;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const uint32_t z = __shfl_down_sync(0xffffffffu, y, off);
-            if (lane + off < 32) y += z;
-        }
-        const uint32_t carry = y - tot;  // chunks above this lane's
-#pragma unroll
-        for (int b = 0; b < 4; ++b) rc[b] += carry;
-#pragma unroll
-        for (int k = 0; k < CH; ++k) {
-            x[k] += rc[k / RUN];  // nT = -T
-            a[k] -= x[k];         // lo = out_0 + T
-        }
-        store_chunk<CH>(s0, c0, a);
-        const uint32_t nt0 = __shfl_sync(0xffffffffu, x[0], 0);
-        const int r = S & 3, sa = S - r;
-        const int fill_from = S - base;  // hi[i] = nT[0] for S - base <= i < S, 0 below
-        uint32_t e[CH];
-        realign_any<CH>(r, x, lane, sa, nt0, fill_from, e);  // hi over [c0 + sa, c0 + sa + CH)
-        store_chunk<CH>(s1, c0 + sa, e);
-        // positions [0, sa) of hi lie below S
-        for (int v = lane; 4 * v < sa; v += 32) {
-            uint32_t f[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) f[k] = 4 * v + k >= fill_from ? nt0 : 0u;
-            sts4(s1, 4 * v, make_uint4(f[0], f[1], f[2], f[3]));
-        }
-        if (J > 0 || !direct) {
-            __syncthreads();
-        } else {
-            // Stage 0 of the group: lo is input row a(2p), hi input row a(2p + 1).
-            // Values below LO must vanish; [dlt, W) of both rows leaves by two
-            // bulk copies once this warp's writes are visible to the async proxy.
-            __syncwarp();
-            for (int i = 4 * lane; i < LO; i += 128) {
-                const uint4 u0 = lds4(s0, i), u1 = lds4(s1, i);
-                const uint32_t e0[4] = {u0.x | u1.x, u0.y | u1.y, u0.z | u1.z, u0.w | u1.w};
-#pragma unroll
-                for (int k = 0; k < 4; ++k) bad |= i + k < LO && e0[k] != 0u;
-            }
-            tma::fence_proxy_async_shared();
-            __syncwarp();
-            if (lane == 0) {
-                const int ua = sg + ((2 * p) << m0) + (wq << (m0 + G));
-                const int ub = ua + (1 << m0);
-                uint32_t *da, *db;
-                if (!L.scatter) {
-                    uint32_t* out = static_cast<uint32_t*>(L.out);
-                    da = out + ((long long)ua * rs_axis + (long long)j * rs_other) * L.gout.pitch;
-                    db = out + ((long long)ub * rs_axis + (long long)j * rs_other) * L.gout.pitch;
-                } else {
-                    uint32_t* vol = static_cast<uint32_t*>(L.out);
-                    const long long ra = M.o0 + (L.axis == 0 ? (long long)ua * M.sx + (long long)j * M.sy
-                                                             : (long long)j * M.sx + (long long)ua * M.sy);
-                    da = vol + ra;
-                    db = vol + ra + (L.axis == 0 ? M.sx : M.sy) * (long long)(1 << m0);
-                }
-                tma::bulk_store(da, s0 + dlt, (W - dlt) * 4u);
-                tma::bulk_store(db, s1 + dlt, (W - dlt) * 4u);
-                tma::bulk_commit();
-                tma::bulk_wait_read();  // shared memory stays valid until the copies have read it
-            }
-        }
+    {
+        InvCtx C;
+        C.rows = rows_al;
+        C.RS = RS; C.W = W; C.base = base; C.sg = sg; C.wq = wq; C.j = j; C.m0 = m0;
+        C.c0 = c0; C.lane = lane; C.warp = warp; C.LO = LO; C.dlt = dlt;
+        C.rs_axis = rs_axis; C.rs_other = rs_other;
+        C.direct = direct;
+        inv_stages<G, VPL, G - 1>(L, C, bad);
     }
 
     if (!direct) {
@@ -670,7 +708,7 @@ planes_inv_group(const __grid_constant__ InvLaunch L) {
                 const int a = sg + (u << m0) + (wq << (m0 + G));
                 const int xp = L.axis == 0 ? a : j, yp = L.axis == 0 ? j : a;
                 const long long rb = M.o0 + xp * M.sx + yp * M.sy;
-                const uint32_t* srow = rows_al + phys_slot<G>(u, 0) * RS;
+                const uint32_t* srow = rows_al + phys_slot<G, 0>(u) * RS;
                 for (int i = lane; i < W; i += 32) {
                     const int d = base + i;
                     const uint32_t e = srow[i];
@@ -684,7 +722,7 @@ planes_inv_group(const __grid_constant__ InvLaunch L) {
             for (int idx = threadIdx.x; idx < R * W; idx += NT) {
                 const int i = idx / R, u = idx - i * R;
                 const int d = base + i;
-                const uint32_t e = rows_al[phys_slot<G>(u, 0) * RS + i];
+                const uint32_t e = rows_al[phys_slot<G, 0>(u) * RS + i];
                 if (d < 2 * N) {
                     bad |= e != 0u;
                 } else {
