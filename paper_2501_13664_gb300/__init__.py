@@ -467,9 +467,45 @@ class PlanesTransform(torch.autograd.Function):
         return planes_adjoint(grad_out.contiguous(), ctx.mask), None
 
 
+class PlanesTransformBatch(torch.autograd.Function):
+    """``PlanesTransform`` over a leading batch dimension.
+
+    Each volume's transform is written straight into its slice of one
+    (B, k, N, N, 3N) output, and backward backprojects each cotangent slice
+    into its slice of one (B, N, N, N) gradient: no stacking or splitting
+    copies of the multi-GB transforms.
+    """
+
+    @staticmethod
+    def forward(ctx, vols: torch.Tensor, dodecants: int = ALL):
+        if vols.dtype != torch.float32:
+            raise TypeError("PlanesTransformBatch needs float32 volumes")
+        if vols.dim() != 4:
+            raise ValueError(f"expected (B, N, N, N) volumes, got {tuple(vols.shape)}")
+        vols = vols.contiguous()
+        B, N = int(vols.shape[0]), int(vols.shape[1])
+        m = _mask(dodecants)
+        ctx.mask = m
+        out = torch.empty((B, _count(m), N, N, 3 * N), dtype=torch.float32, device=vols.device)
+        ws = get_plan(N, torch.float32).workspace("planes_forward")
+        for b in range(B):
+            planes_forward(vols[b], m, out=out[b], workspace=ws)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out: torch.Tensor):
+        g = grad_out.contiguous()
+        B, N = int(g.shape[0]), int(g.shape[2])
+        grad = torch.empty((B, N, N, N), dtype=torch.float32, device=g.device)
+        ws = get_plan(N, torch.float32).workspace("planes_adjoint")
+        for b in range(B):
+            planes_adjoint(g[b], ctx.mask, out=grad[b], workspace=ws)
+        return grad, None
+
+
 def planes(vol: torch.Tensor, dodecants=ALL) -> torch.Tensor:
     """Autograd-aware forward for float32 volumes (batched over a leading dim)."""
     m = _mask(dodecants)
     if vol.dim() == 4:
-        return torch.stack([PlanesTransform.apply(v, m) for v in vol])
+        return PlanesTransformBatch.apply(vol, m)
     return PlanesTransform.apply(vol, m)

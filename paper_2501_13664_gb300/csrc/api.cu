@@ -248,8 +248,10 @@ static size_t djt_adj_slot_bytes(int N) {
     return djt_adj_stage_bytes(N, n - 1) + (n >= 2 ? djt_adj_stage_bytes(N, n - 2) : 0);
 }
 
-static size_t planes_buf_bytes(const drt3d_plan* P) {
-    return align_up(P->planes.buf_elems * 4, 256);
+// One intermediate buffer of the planes adjoint: a fused pass's 32-bit rows,
+// or the dodecant's frame volume that the last pass writes.
+static size_t adjoint_buf_bytes(const drt3d_plan* P) {
+    return std::max(P->fused.buf_bytes, align_up((size_t)P->N * P->N * P->N * 4, 256));
 }
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -474,7 +476,7 @@ static PressLayout press_layout(const drt3d_plan* P) {
     Lo.b = take((size_t)N * N * N * 4);
     Lo.partial = take(kPressNormParts * sizeof(double));
     Lo.norm = take(sizeof(double));
-    Lo.tws_bytes = std::max((size_t)kMaxSlots * 2 * P->fused.buf_bytes, (size_t)kMaxSlots * 2 * planes_buf_bytes(P));
+    Lo.tws_bytes = std::max((size_t)kMaxSlots * 2 * P->fused.buf_bytes, (size_t)kMaxSlots * 2 * adjoint_buf_bytes(P));
     Lo.tws = take(Lo.tws_bytes);
     Lo.total = off;
     return Lo;
@@ -485,7 +487,7 @@ drt3d_status drt3d_workspace_bytes(const drt3d_plan* P, int op, size_t* bytes) {
     switch (op) {
     case DRT3D_OP_PLANES_FORWARD:
     case DRT3D_OP_PLANES_ADJOINT:
-        *bytes = (size_t)kMaxSlots * 2 * (op == DRT3D_OP_PLANES_FORWARD ? P->fused.buf_bytes : planes_buf_bytes(P));
+        *bytes = (size_t)kMaxSlots * 2 * (op == DRT3D_OP_PLANES_FORWARD ? P->fused.buf_bytes : adjoint_buf_bytes(P));
         return DRT3D_OK;
     case DRT3D_OP_PLANES_INVERSE:
         *bytes = 2 * inverse_buf_bytes(P->N);
@@ -619,72 +621,62 @@ drt3d_status drt3d_planes_adjoint(const drt3d_plan* P, const void* d_cot, void* 
     if (P->dtype != DRT3D_I32 && P->dtype != DRT3D_F32) return DRT3D_ERR_DTYPE;
     if (mask == 0 || (mask & ~DRT3D_ALL_DODECANTS)) return DRT3D_ERR_INVALID_ARG;
     if (!aligned16(d_cot) || !aligned16(d_vol) || !aligned16(d_ws)) return DRT3D_ERR_ALIGN;
-    const size_t buf = planes_buf_bytes(P);
+    const size_t buf = adjoint_buf_bytes(P);
     const int nslots = popcount12(mask);
     if (!d_ws || ws_bytes < (size_t)nslots * 2 * buf) return DRT3D_ERR_WORKSPACE;
     const int N = P->N;
     const bool is_float = P->dtype == DRT3D_F32;
     const size_t cot_block = (size_t)N * N * 3 * N * 4;
-    const PlanesSchedule& S = P->planes;
+    const FusedSchedule& S = P->fused;
     char* ws = static_cast<char*>(d_ws);
 
-    PassLaunch L{};
+    FusedLaunch L{};
     L.N = N;
     L.n = P->n;
     L.dmax = 3 * N;
-    // Stage counts before each forward pass (for the byte accounting).
-    int mxs[kMaxPasses], mys[kMaxPasses];
-    for (int p = 0, mx = 0, my = 0; p < S.npass; ++p) {
-        mxs[p] = mx; mys[p] = my;
-        if (S.pass[p].axis == 0) mx += S.pass[p].G; else my += S.pass[p].G;
-    }
-    // Passes in reverse; q counts adjoint passes done so the ping-pong is
-    // independent of the forward parity.
+    L.status = P->d_status;
+    // The fused forward passes transposed, last first; q counts adjoint passes
+    // done so the ping-pong of buffers is independent of the pass count.
     for (int p = S.npass - 1, q = 0; p >= 0; --p, ++q) {
-        const PassSpec& ps = S.pass[p];
-        L.axis = ps.axis;
+        const FusedPass& ps = S.pass[p];
         L.m0 = ps.m0;
-        L.gin = ps.in;
-        L.gout = ps.out;
-        L.V = warp_tile_valid(ps.G);
-        const int e_lo = (p == 0) ? 2 * N : ps.in.base;
-        const int span = 3 * N - e_lo + ((1 << ps.m0) - 1) * ((1 << ps.G) - 1);
-        L.ntiles = (span + L.V - 1) / L.V;
-        L.warps = ((long long)N << (P->n - ps.G)) * L.ntiles;
-        auto fill = [&](int i) {
+        L.gin = ps.out;                                // the forward pass's output rows
+        L.gout = p == 0 ? Geo{2 * N, N} : ps.in;       // its input rows, or the frame volume
+        int V = 0, PB = 0;
+        adjoint_fused_tile(ps.G, &V, &PB);
+        L.V = V;
+        const int R1 = (1 << ps.G) - 1;
+        const int off_max = 2 * ((1 << ps.m0) - 1) * R1;
+        const int dfirst = (L.gout.base - PB - off_max) & ~3;
+        L.ntiles = (3 * N - PB - dfirst + V - 1) / V;
+        const long long per_axis = 1LL << (P->n - ps.G);
+        L.ctas = per_axis * per_axis * L.ntiles;
+        FramesSum FS{};
+        for (int k = 0, i = 0; k < 12; ++k) {
+            if (!((mask >> k) & 1)) continue;
             char* bufA = ws + (size_t)i * 2 * buf;
             char* bufB = bufA + buf;
-            SlotPtrs& sp = L.slot[i];
-            sp.in = (q == 0) ? (const void*)(static_cast<const char*>(d_cot) + (size_t)i * cot_block)
+            FusedSlot& fs = L.slot[i];
+            fs.in = (q == 0) ? (const void*)(static_cast<const char*>(d_cot) + (size_t)i * cot_block)
                              : ((q & 1) ? (const void*)bufA : (const void*)bufB);
-            sp.out = (q & 1) ? (void*)bufB : (void*)bufA;
-        };
-        if (p > 0) {
-            for (int i = 0; i < nslots; ++i) fill(i);
-            char nm[40];
-            std::snprintf(nm, sizeof nm, "planes_adj_pass %c G=%d m0=%d", ps.axis ? 'y' : 'x', ps.G, ps.m0);
-            prof_begin(P, stream, nm, nslots * planes_pass_bytes(P, ps, mxs[p], mys[p], true));
-            if (launch_planes_adjoint_pass(L, ps.G, is_float, nslots, stream) != cudaSuccess)
-                return DRT3D_ERR_CUDA;
-            prof_end(P, stream);
-        } else {
-            // Every dodecant's frame volume F_k[x'][y'][z'] (rows d in [2N, 3N))
-            // into the buffer this pass does not read, in one launch; then their
-            // sum through the dodecant maps, added in increasing k so that the
-            // float sum has a fixed order.
-            FramesSum FS{};
-            for (int k = 0, i = 0; k < 12; ++k) {
-                if (!((mask >> k) & 1)) continue;
-                fill(i);
-                FS.frame[i] = L.slot[i].out;
+            fs.out = (q & 1) ? (void*)bufB : (void*)bufA;
+            if (p == 0) {
+                FS.frame[i] = fs.out;
                 frames_sum_axes(dodecant_affine(N, k), N, i, &FS);
-                ++i;
             }
-            L.gin = Geo{2 * N, N};  // rows d in [2N, 3N), pitch N: the frame F[x'][y'][z']
-            prof_begin(P, stream, "planes_adj_frames", nslots * planes_pass_bytes(P, ps, 0, 0, true));
-            if (launch_planes_adjoint_pass(L, ps.G, is_float, nslots, stream) != cudaSuccess)
-                return DRT3D_ERR_CUDA;
-            prof_end(P, stream);
+            ++i;
+        }
+        char nm[40];
+        std::snprintf(nm, sizeof nm, "planes_adj_fused G=%d m0=%d", ps.G, ps.m0);
+        const double lo_in = 2.0 * N + 2 - 2.0 * (1 << ps.m0), lo_out = 2.0 * N + 2 - 2.0 * (1 << (ps.m0 + ps.G));
+        const double rd = ps.final_ ? (double)N * N * 3 * N * 4 : (double)N * N * (3 * N - lo_out) * 4;
+        const double wr = p == 0 ? (double)N * N * N * 4 : (double)N * N * (3 * N - lo_in) * 4;
+        prof_begin(P, stream, nm, nslots * (rd + wr));
+        if (launch_planes_adjoint_fused(L, ps.G, is_float, nslots, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+        prof_end(P, stream);
+        if (p == 0) {
+            // the frames summed through the dodecant maps, in increasing k so
+            // that the float sum has a fixed order
             FS.vol = d_vol;
             FS.N = N;
             FS.nslots = nslots;

@@ -162,6 +162,7 @@ struct FusedLaunch {
     int vec_store;   // output rows allow aligned vector stores
     int* status;     // device status word (time-outs of staged loads), may be null
     int global_layout;  // last pass writes Algorithm 2's 4N x 4N x (3N - 2) array
+    int prefetch_ahead;  // CTAs (in launch order) whose input rows a CTA prefetches into L2, 0 = none
 };
 
 // One fused pass: G stages of eq.(map3D) (both axes).
@@ -301,6 +302,12 @@ cudaError_t launch_planes_fused_tma(const FusedLaunch& L, int G, ElemKind out_ki
 // z = slot), for launches that keep it in global memory.
 cudaError_t encode_fused_tmap(const FusedLaunch& L, const void* in_base, size_t slot_stride, int nslots,
                               CUtensorMap* map);
+// The transpose of one fused pass (planes_adjoint_fused.cu): reads the
+// forward pass's output rows (geometry gin) as cotangent and writes its input
+// rows (geometry gout; the frame volume, base 2N and pitch N, for the first
+// pass).  `V` stored positions per tile; tile origins are placed by the kernel.
+void adjoint_fused_tile(int G, int* V, int* PB);
+cudaError_t launch_planes_adjoint_fused(const FusedLaunch& L, int G, bool is_float, int nslots, cudaStream_t s);
 cudaError_t launch_planes_pass(const PassLaunch& L, int G, drt3d_dtype in_dtype, bool ingest,
                                bool is_float, int nslots, cudaStream_t s);
 cudaError_t launch_planes_adjoint_pass(const PassLaunch& L, int G, bool is_float, int nslots, cudaStream_t s);

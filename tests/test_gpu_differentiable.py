@@ -79,6 +79,21 @@ def test_autograd_batched_and_subset(drt):
     assert torch.allclose(x.grad[1], want, rtol=1e-6, atol=1e-4)
 
 
+def test_batched_function_matches_single_volume_calls(drt):
+    """The batched autograd function writes each volume's transform into its
+    slice and backprojects each cotangent slice: bit for bit the single-volume
+    forward and adjoint, N = 32, batch 3, all dodecants."""
+    N, B = 32, 3
+    x = torch.from_numpy(synth.random_float((B, N, N, N), 530)).cuda().requires_grad_(True)
+    y = drt.planes(x)
+    assert y.shape == (B, 12, N, N, 3 * N)
+    r = torch.from_numpy(synth.random_float((B, 12, N, N, 3 * N), 531)).cuda()
+    (y * r).sum().backward()
+    for i in range(B):
+        assert torch.equal(y[i], drt.planes_forward(x[i].detach()))
+        assert torch.equal(x.grad[i], drt.planes_adjoint(r[i]))
+
+
 def test_lsq_trajectory_against_fp64_oracle(drt, oracle_mod):
     """50 steps of gradient descent (step 1/L) at N = 32, batch 2, against the
     same iteration run with the oracle's FP64 forward and backprojection."""
