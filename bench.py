@@ -215,6 +215,68 @@ def _oracle_inverse(k: int) -> float:
     return time.perf_counter() - t0
 
 
+def _oracle_c4_volume(args) -> float:
+    """All 12 dodecants of one batch volume (Algorithm 1); seconds."""
+    import oracle
+
+    f, = args
+    t0 = time.perf_counter()
+    oracle.planes_forward(f)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_extras(f_np, workers: int) -> dict:
+    """The rest of the CPU baseline: the N=256 step single-threaded, one DJT
+    sector at N=128 (x12, extrapolated), and the 96-volume mixed batch over
+    the pool.  Run after the GPU work, on the host cores."""
+    import multiprocessing as mp
+
+    import oracle
+    import synth
+
+    oracle.build()
+    out = {}
+    # single process: the 12 dodecant forwards one after another, then the inverse
+    t0 = time.perf_counter()
+    R0 = None
+    for k in range(12):
+        R = oracle.planes_forward(f_np, dodecants=[k])[0]
+        if k == 0:
+            R0 = R
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.planes_inverse(R0, 0)
+    t_inv = time.perf_counter() - t0
+    del R, R0
+    out["single_thread"] = {"value": 1.0 / (t_fwd + t_inv), "unit": UNIT, "threads": 1,
+                            "sample": f"one full step in one process: Algorithm 1 on the 12 dodecants "
+                                      f"({t_fwd:.2f} s) + the exact inverse of dodecant 0 ({t_inv:.2f} s)"}
+    # lines: one sector of the config-3 volume, extrapolated to 12
+    f3 = synth.c3_volume(128)
+    t0 = time.perf_counter()
+    oracle.lines_forward(f3, [0])
+    t_sec = time.perf_counter() - t0
+    out["lines_c3"] = {"sector_s": t_sec, "twelve_sectors_s": 12 * t_sec, "extrapolated": True, "threads": 1,
+                       "value": 1.0 / (12 * t_sec), "unit": "volumes/s",
+                       "sample": "Algorithm 3 on sector 0 of the N=128 int16 volume (32 lines), one process; "
+                                 "the 12-sector time is that sector's time x 12 (extrapolated)"}
+    # the mixed batch: each volume's 12 dodecants is one task of the pool
+    vols = synth.c4_batch()
+    order = sorted(range(len(vols)), key=lambda i: -vols[i].shape[0])
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        pool.map(_oracle_c4_volume, [(vols[i],) for i in order[-workers:]])  # warm the workers
+        t0 = time.perf_counter()
+        pool.map(_oracle_c4_volume, [(vols[i],) for i in order], chunksize=1)
+        t_b = time.perf_counter() - t0
+    out["batched_c4"] = {"s": t_b, "value": len(vols) / t_b, "unit": "volumes/s", "processes": workers,
+                         "sample": f"the {len(vols)} uint8 volumes of the mixed batch (N 16..256), Algorithm 1 on "
+                                   f"all 12 dodecants of each, one volume per task over {workers} processes, "
+                                   "largest first"}
+    out["host_cores"] = os.cpu_count()
+    return out
+
+
 def oracle_pool(f_u8):
     """A pool of oracle worker processes on the host cores (spawned: safe after
     CUDA initialisation), one per dodecant at most, with the volume loaded."""
@@ -473,6 +535,8 @@ def run_ours(args):
                   f"{workers} processes ({t_fwd:.2f} s wall) + the exact inverse of dodecant 0 ({t_inv:.2f} s)")
         line["cpu_baseline"] = {"value": 1.0 / (t_fwd + t_inv), "unit": UNIT, "cores": workers, "kind": "oracle",
                                 "sample": sample}
+        if not args.no_extras:
+            line["cpu_baseline"].update(cpu_baseline_extras(f_np, workers))
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -44,17 +44,29 @@ planes_fused(const __grid_constant__ FusedLaunch L) {
 }
 
 template <typename TIn, typename TOut, typename T, typename TS, int G, bool INGEST>
-cudaError_t launch_g(const FusedLaunch& L, int nslots, cudaStream_t s) {
+cudaError_t launch_g(const FusedLaunch& Lin, int nslots, cudaStream_t s) {
     const size_t smem = ((size_t)(1 << (2 * G)) * fused_ws<G>() + K) * sizeof(TS);
     auto kern = planes_fused<TIn, TOut, T, TS, G, INGEST>;
-    static DeviceOnce attr_done;  // per instantiation
+    static DeviceOnce attr_done;           // per instantiation
+    static std::atomic<int> wave[64] = {};  // resident CTAs of the device, written before the flag
     int dev = 0;
-    cudaGetDevice(&dev);
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_done.done(dev)) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+        int sms = 0, per = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * fused_warps<G>(), smem);
+        if (e != cudaSuccess) return e;
+        wave[dev].store(per * sms, std::memory_order_relaxed);
         attr_done.mark(dev);
     }
+    FusedLaunch L = Lin;
+    // 32-bit buffer input read by the register loader: prefetch one wave ahead
+    L.prefetch_ahead = (!INGEST && sizeof(TIn) == 4) ? wave[dev].load(std::memory_order_relaxed) : 0;
     dim3 grid((unsigned)L.ctas, (unsigned)nslots);
     kern<<<grid, 32 * fused_warps<G>(), smem, s>>>(L);
     return cudaGetLastError();
