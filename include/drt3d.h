@@ -159,6 +159,25 @@ drt3d_status drt3d_planes_forward(const drt3d_plan* plan, const void* d_in, void
 drt3d_status drt3d_planes_forward_global(const drt3d_plan* plan, const void* d_in, void* d_out, void* d_ws,
                                          size_t ws_bytes, cudaStream_t stream);
 
+/* Residual of the planes forward against a target: d_out = A d_in - d_target
+ * cell by cell, with A the transform of drt3d_planes_forward (same inputs,
+ * masks, workspace and layouts).  The subtraction happens as the last pass
+ * stores each cell, so the transform itself is never written out: this is
+ * the residual of the least-squares fit of a volume to a target transform
+ * (the gradient of 0.5 ||A x - b||^2 is the adjoint of the residual).
+ *   d_target : popcount(dodecant_mask) blocks of N*N*3N elements of the output
+ *              type, R[k][s1][s2][d] layout, 16-byte aligned; it may be d_out
+ *              itself (each cell is read before it is overwritten by the same
+ *              thread).
+ * Float32 results equal the forward's cell minus the target cell rounded once
+ * (bit for bit the forward followed by a subtraction); integer results wrap.
+ * The paper has no counterpart: its method stops at the transform and its
+ * backprojection.
+ * Errors: as drt3d_planes_forward; INVALID_ARG when d_target is NULL. */
+drt3d_status drt3d_planes_forward_residual(const drt3d_plan* plan, const void* d_in, const void* d_target,
+                                           void* d_out, uint32_t dodecant_mask, void* d_ws, size_t ws_bytes,
+                                           cudaStream_t stream);
+
 /* Adjoint (backprojection) of drt3d_planes_forward (Section 5.1, stage loop
  * reversed with eq.(invmap3Dsummation); reads below d = 0 are zero):
  *   d_vol = sum over selected k, in increasing k, of g_k^T(A_k^T d_cot[k]).

@@ -242,6 +242,28 @@ def planes_forward(vol: torch.Tensor, dodecants=ALL, out: torch.Tensor | None = 
     return out
 
 
+def planes_forward_residual(vol: torch.Tensor, target: torch.Tensor, dodecants=ALL,
+                            out: torch.Tensor | None = None, workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """A vol - target over the selected dodecants, the subtraction done as the
+    transform's last pass stores each cell (``target`` in the output layout;
+    ``out`` may be ``target`` itself)."""
+    vol_d, host = _to_device(vol)
+    N = _vol_check(vol_d)
+    m = _mask(dodecants)
+    plan = get_plan(N, vol_d.dtype)
+    odt = torch.float32 if vol_d.dtype == torch.float32 else torch.int32
+    shape = (_count(m), N, N, 3 * N)
+    if tuple(target.shape) != shape or target.dtype != odt or not target.is_cuda or not target.is_contiguous():
+        raise ValueError(f"target must be a contiguous cuda {odt} tensor of shape {shape}")
+    if out is None:
+        out = torch.empty(shape, dtype=odt, device=vol_d.device)
+    ws = workspace if workspace is not None else plan.workspace("planes_forward")
+    _abi.check(plan._lib.drt3d_planes_forward_residual(plan.handle, vol_d.data_ptr(), target.data_ptr(),
+                                                       out.data_ptr(), m, ws.data_ptr(), ws.numel(), _stream()),
+               "drt3d_planes_forward_residual")
+    return out.to("cpu") if host else out
+
+
 def planes_forward_global(vol: torch.Tensor, out: torch.Tensor | None = None,
                           workspace: torch.Tensor | None = None) -> torch.Tensor:
     """All 12 dodecants in Algorithm 2's global 4N x 4N x (3N-2) layout."""

@@ -28,6 +28,7 @@ SIGNATURES = {
     "drt3d_lines_out_shape": (I, [P, I64P]),
     "drt3d_workspace_bytes": (I, [P, I, ctypes.POINTER(SZ)]),
     "drt3d_planes_forward": (I, [P, P, P, U32, P, SZ, P]),
+    "drt3d_planes_forward_residual": (I, [P, P, P, P, U32, P, SZ, P]),
     "drt3d_planes_adjoint": (I, [P, P, P, U32, P, SZ, P]),
     "drt3d_planes_inverse": (I, [P, P, I, P, P, SZ, P]),
     "djt3d_lines_forward": (I, [P, P, P, U32, P, SZ, P]),

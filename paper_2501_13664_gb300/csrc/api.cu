@@ -535,8 +535,10 @@ static void global_row_map(int N, int k, FusedSlot& fs) {
 }
 
 static drt3d_status planes_forward_impl(const drt3d_plan* P, const void* d_in, void* d_out, uint32_t mask,
-                                        void* d_ws, size_t ws_bytes, cudaStream_t stream, bool global) {
+                                        void* d_ws, size_t ws_bytes, cudaStream_t stream, bool global,
+                                        const void* d_sub = nullptr) {
     if (!P || !d_in || !d_out) return DRT3D_ERR_INVALID_ARG;
+    if (d_sub && (global || !aligned16(d_sub))) return d_sub && global ? DRT3D_ERR_INVALID_ARG : DRT3D_ERR_ALIGN;
     if (!device_is_current(P->device)) return DRT3D_ERR_INVALID_ARG;
     if (mask == 0 || (mask & ~DRT3D_ALL_DODECANTS)) return DRT3D_ERR_INVALID_ARG;
     if (!aligned16(d_in) || !aligned16(d_out) || !aligned16(d_ws)) return DRT3D_ERR_ALIGN;
@@ -565,6 +567,8 @@ static drt3d_status planes_forward_impl(const drt3d_plan* P, const void* d_in, v
             fs.in = (p == 0) ? d_in : ((p & 1) ? (const void*)bufA : (const void*)bufB);
             fs.out = ps.final_ ? (void*)(static_cast<char*>(d_out) + (global ? 0 : (size_t)i * out_block))
                                : ((p & 1) ? (void*)bufB : (void*)bufA);
+            fs.sub = (ps.final_ && d_sub) ? (const void*)(static_cast<const char*>(d_sub) + (size_t)i * out_block)
+                                          : nullptr;
             if (global) global_row_map(N, k, fs);
             ++i;
         }
@@ -594,6 +598,12 @@ static drt3d_status planes_forward_impl(const drt3d_plan* P, const void* d_in, v
 drt3d_status drt3d_planes_forward(const drt3d_plan* P, const void* d_in, void* d_out, uint32_t mask,
                                   void* d_ws, size_t ws_bytes, cudaStream_t stream) {
     return planes_forward_impl(P, d_in, d_out, mask, d_ws, ws_bytes, stream, false);
+}
+
+drt3d_status drt3d_planes_forward_residual(const drt3d_plan* P, const void* d_in, const void* d_target, void* d_out,
+                                           uint32_t mask, void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!d_target) return DRT3D_ERR_INVALID_ARG;
+    return planes_forward_impl(P, d_in, d_out, mask, d_ws, ws_bytes, stream, false, d_target);
 }
 
 drt3d_status drt3d_planes_forward_global(const drt3d_plan* P, const void* d_in, void* d_out, void* d_ws,

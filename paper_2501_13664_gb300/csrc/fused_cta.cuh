@@ -237,6 +237,33 @@ __device__ __forceinline__ void store_rows(const FusedLaunch& L, const FusedSlot
     TOut* out = static_cast<TOut*>(sp.out) + (d - L.gout.base);
     const long long rstride = (long long)rs2 * L.gout.pitch;
     TOut* dst = out + orow0 * L.gout.pitch;
+    // residual epilogue: the target cell at the same offset as the output's
+    const TOut* sub = sp.sub ? static_cast<const TOut*>(sp.sub) + (dst - static_cast<TOut*>(sp.out)) : nullptr;
+    if constexpr (sizeof(TOut) == 4) {
+        if (sub && L.vec_store) {
+            // The target rows are read in batches of up to 8 before the batch's
+            // stores (the target may be the output itself, so a store may not
+            // pass a later row's read: reading first keeps the loads in flight).
+            constexpr int BT = R < 8 ? R : 8;
+#pragma unroll
+            for (int t0 = 0; t0 < R; t0 += BT) {
+                uint4 bw[BT];
+#pragma unroll
+                for (int j = 0; j < BT; ++j) bw[j] = __ldcs(reinterpret_cast<const uint4*>(sub + (long long)(t0 + j) * rstride));
+#pragma unroll
+                for (int j = 0; j < BT; ++j) {
+                    TOut e[K], b[K];
+                    memcpy(b, &bw[j], 16);
+#pragma unroll
+                    for (int i = 0; i < K; ++i) e[i] = (TOut)v[t0 + j][i] - b[i];
+                    uint4 w;
+                    memcpy(&w, e, 16);
+                    st_global(reinterpret_cast<uint4*>(dst + (long long)(t0 + j) * rstride), w);
+                }
+            }
+            return;
+        }
+    }
     if (L.vec_store) {
 #pragma unroll
         for (int t2 = 0; t2 < R; ++t2, dst += rstride) {
@@ -258,7 +285,11 @@ __device__ __forceinline__ void store_rows(const FusedLaunch& L, const FusedSlot
         for (int t2 = 0; t2 < R; ++t2, dst += rstride)
 #pragma unroll
             for (int i = 0; i < K; ++i)
-                if (d + i < L.dmax) st_global(dst + i, (TOut)v[t2][i]);
+                if (d + i < L.dmax) {
+                    TOut e = (TOut)v[t2][i];
+                    if (sub) e = e - sub[(long long)t2 * rstride + i];
+                    st_global(dst + i, e);
+                }
     }
 }
 
@@ -301,6 +332,19 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
     // skip the loads and both transforms.
     const int smax1 = (sg1 << G) + (1 << G) - 1, smax2 = (sg2 << G) + (1 << G) - 1;
     const bool zero_tile = d0 + L.V <= 2 * N - smax1 - smax2;
+
+    if (sp.sub && threadIdx.x < R * R && sizeof(TOut) == 4 && L.vec_store) {
+        // Residual: warm L2 with this tile's target rows (one row window per
+        // thread), read again by the stores at the end of phase 2.
+        const int t1 = threadIdx.x / R, t2 = threadIdx.x % R;
+        const int o1 = t1 + (sg1 << G) + (wq1 << (m0 + G)), o2 = t2 + (sg2 << G) + (wq2 << (m0 + G));
+        const int hi = min(d0 + L.V, L.dmax);
+        if (d0 < hi)
+            tma::prefetch_l2(static_cast<const TOut*>(sp.sub) +
+                                 ((long long)o1 * rs1 + (long long)o2 * rs2) * L.gout.pitch + (d0 - L.gout.base),
+                             (uint32_t)(hi - d0) * (uint32_t)sizeof(TOut));
+    }
+
 
     if (zero_tile) {
         if (!active) return;

@@ -148,6 +148,9 @@ struct FusedSlot {
     // g0 + s1 g1 + s2 g2 of the 4N x 4N x (3N - 2) array.
     long long g0;
     int g1, g2;
+    // Final pass only: when set, each output cell is stored minus the cell at
+    // the same offset of this array (the residual of a least-squares fit).
+    const void* sub;
 };
 
 struct FusedLaunch {

@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(32 * fused_warps<G>(), (G >= 4 ? 2 : 1))
 planes_fused(const __grid_constant__ FusedLaunch L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if constexpr (INGEST && G == 4 && std::is_same<TIn, uint8_t>::value && std::is_same<TS, uint16_t>::value) {
-        if (!L.global_layout)  // 16-bit sums: two groups per register
+        if (!L.global_layout && !L.slot[blockIdx.y].sub)  // 16-bit sums: two groups per register
             fused_cta_u8x2<TOut, G>(L, L.slot[blockIdx.y], blockIdx.x, smem_raw);
         else
             fused_cta<TIn, TOut, T, TS, G, INGEST, false>(L, L.slot[blockIdx.y], blockIdx.x, smem_raw);

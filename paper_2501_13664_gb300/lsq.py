@@ -1,8 +1,9 @@
 """Least-squares fit of volumes to target planes transforms by gradient descent.
 
 The planes transform A (all 12 dodecants) is linear; its gradient is the
-hand-written adjoint (backprojection of Section 5.1) through
-``PlanesTransform``.  ``fit`` minimises 0.5 * ||A x - b||^2 from x = 0 with
+hand-written adjoint (backprojection of Section 5.1).  ``LeastSquaresLoss``
+computes the residual A x - b inside the transform's last pass and
+backprojects it; ``fit`` minimises 0.5 * ||A x - b||^2 from x = 0 with
 the fixed step 1 / L, L = sigma_max(A)^2 estimated by power iteration on
 A^T A (the step that makes plain gradient descent monotone on this convex
 quadratic).
@@ -11,7 +12,51 @@ from __future__ import annotations
 
 import torch
 
-from . import ALL, planes, planes_adjoint, planes_forward
+from . import ALL, _mask, get_plan, planes_adjoint, planes_forward, planes_forward_residual
+
+
+class LeastSquaresLoss(torch.autograd.Function):
+    """0.5 ||A x - b||^2 over a batch, with A the planes transform.
+
+    Forward computes the residual r = A x - b in the transform's own store
+    (one pass over b, none over A x) and the loss from r; backward is the
+    hand-written adjoint (backprojection) of r, scaled by the incoming
+    gradient.  r is kept between the two (the one tensor of the size of b).
+    """
+
+    @staticmethod
+    def forward(ctx, x: torch.Tensor, b: torch.Tensor, dodecants: int = ALL):
+        if x.dtype != torch.float32 or x.dim() != 4:
+            raise TypeError("expected (B, N, N, N) float32 volumes")
+        x = x.contiguous()
+        B, N = int(x.shape[0]), int(x.shape[1])
+        m = _mask(dodecants)
+        r = torch.empty_like(b)
+        ws = get_plan(N, torch.float32).workspace("planes_forward")
+        for i in range(B):
+            planes_forward_residual(x[i], b[i], m, out=r[i], workspace=ws)
+        ctx.save_for_backward(r)
+        ctx.mask = m
+        # one float32 pass over r (a float64 norm would first copy r to float64)
+        return 0.5 * torch.linalg.vector_norm(r).double() ** 2
+
+    @staticmethod
+    def backward(ctx, g: torch.Tensor):
+        (r,) = ctx.saved_tensors
+        B, N = int(r.shape[0]), int(r.shape[2])
+        grad = torch.empty((B, N, N, N), dtype=torch.float32, device=r.device)
+        ws = get_plan(N, torch.float32).workspace("planes_adjoint")
+        for i in range(B):
+            planes_adjoint(r[i], ctx.mask, out=grad[i], workspace=ws)
+        grad.mul_(g.to(grad.dtype))  # the incoming gradient (1 for loss.backward())
+        return grad, None, None
+
+
+def least_squares_loss(x: torch.Tensor, b: torch.Tensor, dodecants=ALL) -> torch.Tensor:
+    """0.5 ||A x - b||^2 (float64 scalar; the norm of the float32 residual is
+    accumulated in float32) for (B, N, N, N) float32 x and
+    (B, k, N, N, 3N) float32 targets; differentiable in x."""
+    return LeastSquaresLoss.apply(x, b, _mask(dodecants))
 
 
 def operator_norm_sq(N: int, iters: int = 20, seed: int = 0, device=None) -> float:
@@ -40,8 +85,7 @@ def fit(b: torch.Tensor, steps: int = 50, L: float | None = None, dodecants: int
     losses = []
     for _ in range(steps):
         xr = x.detach().requires_grad_(True)
-        r = planes(xr, dodecants) - b
-        loss = 0.5 * (r.double() ** 2).sum()
+        loss = least_squares_loss(xr, b, dodecants)
         loss.backward()
         losses.append(float(loss.detach()))
         x = (xr - xr.grad / L).detach()

@@ -94,6 +94,48 @@ def test_batched_function_matches_single_volume_calls(drt):
         assert torch.equal(x.grad[i], drt.planes_adjoint(r[i]))
 
 
+@pytest.mark.parametrize("N,dt", [(32, torch.float32), (16, torch.int32), (16, torch.uint8), (64, torch.uint8)])
+def test_forward_residual_is_forward_minus_target(drt, N, dt):
+    """drt3d_planes_forward_residual: A x - b subtracted as the last pass
+    stores, bit for bit the forward followed by the subtraction (float32
+    rounding once, integers wrapping); also in place over the target."""
+    mask = [0, 3, 7, 11]
+    if dt == torch.float32:
+        x = torch.from_numpy(synth.random_float((N, N, N), 540 + N)).cuda()
+        b = torch.from_numpy(synth.random_float((4, N, N, 3 * N), 541 + N)).cuda()
+    else:
+        x = torch.from_numpy(synth.random_int32((N, N, N), 540 + N, 0, 256)).to(dt).cuda()
+        b = torch.from_numpy(synth.random_int32((4, N, N, 3 * N), 541 + N)).cuda()
+    want = drt.planes_forward(x, mask) - b
+    assert torch.equal(drt.planes_forward_residual(x, b, mask), want)
+    b2 = b.clone()
+    drt.planes_forward_residual(x, b2, mask, out=b2)
+    assert torch.equal(b2, want)
+
+
+def test_least_squares_loss_matches_autograd_of_mse(drt):
+    """The least-squares autograd function (residual in the forward's store,
+    adjoint of the saved residual) gives the same gradient, bit for bit, as
+    autograd through the batched transform and PyTorch's squared error, and
+    the same loss up to its float64 summation."""
+    from paper_2501_13664_gb300 import lsq
+
+    N, B = 32, 2
+    x = torch.from_numpy(synth.random_float((B, N, N, N), 550)).cuda()
+    b = torch.from_numpy(synth.random_float((B, 12, N, N, 3 * N), 551)).cuda()
+    xa = x.clone().requires_grad_(True)
+    la = 0.5 * torch.nn.functional.mse_loss(drt.planes(xa), b, reduction="sum")
+    la.backward()
+    xb = x.clone().requires_grad_(True)
+    lb = lsq.least_squares_loss(xb, b)
+    lb.backward()
+    assert torch.equal(xa.grad, xb.grad)
+    # the float32 residual, squared and summed in float64; the loss sums in float32
+    ref = 0.5 * float(((drt.planes(x) - b).double() ** 2).sum())
+    assert abs(float(lb.detach()) - ref) <= 1e-5 * ref
+    assert abs(float(la.detach()) - ref) <= 1e-5 * ref
+
+
 def test_lsq_trajectory_against_fp64_oracle(drt, oracle_mod):
     """50 steps of gradient descent (step 1/L) at N = 32, batch 2, against the
     same iteration run with the oracle's FP64 forward and backprojection."""
