@@ -59,39 +59,6 @@ static Geo planes_geo(int N, int mx, int my) {
     return g;
 }
 
-PlanesSchedule make_planes_schedule(int N) {
-    PlanesSchedule S{};
-    const int n = ilog2(N);
-    const int ngroups = (n + 3) / 4;
-    int sizes[8];
-    for (int g = 0; g < ngroups; ++g) sizes[g] = n / ngroups + (g < n % ngroups ? 1 : 0);
-    int mx = 0, my = 0, p = 0;
-    size_t maxel = 0;
-    Geo prev{0, 0};
-    for (int g = 0; g < ngroups; ++g) {
-        for (int axis = 0; axis < 2; ++axis) {
-            PassSpec& P = S.pass[p];
-            P.axis = axis;
-            P.G = sizes[g];
-            P.m0 = axis == 0 ? mx : my;
-            P.in = prev;
-            P.ingest = (p == 0);
-            if (axis == 0) mx += P.G; else my += P.G;
-            P.final_ = (g == ngroups - 1 && axis == 1);
-            P.out = P.final_ ? Geo{0, 3 * N} : planes_geo(N, mx, my);
-            if (!P.final_) {
-                const size_t el = (size_t)N * N * P.out.pitch;
-                if (el > maxel) maxel = el;
-            }
-            prev = P.out;
-            ++p;
-        }
-    }
-    S.npass = p;
-    S.buf_elems = maxel;
-    return S;
-}
-
 static ElemKind kind_of(drt3d_dtype d) {
     switch (d) {
     case DRT3D_U8: return ElemKind::U8;
@@ -262,9 +229,7 @@ static int popcount12(uint32_t m) {
     return c;
 }
 
-constexpr int kLanesK = 4;  // displacements per lane in planes_pass.cu
 
-static int warp_tile_valid(int G) { return (32 * kLanesK - ((1 << G) - 1)) & ~3; }
 
 // Profiling helpers: no-ops unless drt3d_set_profiling(plan, 1).
 static void prof_begin(const drt3d_plan* P, cudaStream_t s, const char* name, double bytes) {
@@ -279,21 +244,6 @@ static void prof_end(const drt3d_plan* P, cudaStream_t s) {
     if (!pr.on || pr.count >= kMaxLaunch) return;
     cudaEventRecord(pr.ev[2 * pr.count + 1], s);
     ++pr.count;
-}
-
-// Algorithmic bytes of one planes pass for one dodecant: the compact rows it
-// must read (d >= lo of its input stage, or the volume) plus the rows it
-// writes (d >= lo of its output stage, or the full public 3N rows).
-static double planes_pass_bytes(const drt3d_plan* P, const PassSpec& ps, int mx0, int my0, bool adjoint) {
-    const double N = P->N;
-    const int mx1 = mx0 + (ps.axis == 0 ? ps.G : 0), my1 = my0 + (ps.axis == 1 ? ps.G : 0);
-    const double lo_in = 2 * N + 2 - (1 << mx0) - (1 << my0);
-    const double lo_out = 2 * N + 2 - (1 << mx1) - (1 << my1);
-    const double item = adjoint ? 4.0 : (P->dtype == DRT3D_U8 ? 1.0 : P->dtype == DRT3D_I16 ? 2.0 : 4.0);
-    const double vol = N * N * N * (ps.ingest ? item : 4.0);
-    const double in_b = ps.ingest ? vol : N * N * (3 * N - lo_in) * 4.0;
-    const double out_b = ps.final_ ? N * N * 3 * N * 4.0 : N * N * (3 * N - lo_out) * 4.0;
-    return in_b + out_b;
 }
 
 // Algorithmic bytes of one fused pass for one dodecant (compact rows read at
@@ -391,7 +341,6 @@ drt3d_status drt3d_plan_create(drt3d_plan** plan, int N, drt3d_dtype in_dtype, u
         delete P;
         return DRT3D_ERR_CUDA;
     }
-    P->planes = make_planes_schedule(N);
     P->fused = make_fused_schedule(N, in_dtype);
     *plan = P;
     return DRT3D_OK;
@@ -436,7 +385,6 @@ static drt3d_plan* level_plan(const drt3d_plan* P, int l) {
         q->device = P->device;
         q->d_status = P->d_status;
         q->borrowed_status = true;
-        q->planes = make_planes_schedule(q->N);
         q->fused = make_fused_schedule(q->N, DRT3D_F32);
         if (P->levels[l].compare_exchange_strong(have, q, std::memory_order_acq_rel))
             return q;

@@ -2,7 +2,7 @@
 // images over up to four quadrants (Section 2.2).
 //
 // The n stages are grouped into passes of G <= 4 stages.  A pass works on
-// units (sg, w) exactly as the one-axis planes passes do (rows sg + 2^m0 v
+// units (sg, w) with the row numbering of internal.cuh (rows sg + 2^m0 v
 // before the pass, new slope bits appended below the old ones after it, so
 // the last pass leaves row s = the paper's slope), one warp per unit and
 // tile of displacements: it loads the unit's 2^G rows sheared by sg * u, runs

@@ -68,23 +68,6 @@ struct Geo {
     int pitch;  // elements per row
 };
 
-// One pass of the planes schedule.
-struct PassSpec {
-    int axis;   // 0: stages along s1 (first index), 1: along s2 (second index)
-    int m0;     // stages already done along this axis
-    int G;      // stages in this pass (1..4)
-    Geo in;     // geometry read (ignored when ingest)
-    Geo out;    // geometry written
-    bool ingest;  // reads the volume through the dodecant map
-    bool final_;  // writes the public output layout
-};
-
-struct PlanesSchedule {
-    int npass;
-    PassSpec pass[kMaxPasses];
-    size_t buf_elems;  // elements of the largest intermediate (one buffer)
-};
-
 // Affine map from a frame coordinate (x', y', z') to a flat index of the
 // original volume: o0 + x' sx + y' sy + z' sz.
 struct Affine {
@@ -96,10 +79,6 @@ struct Affine {
 Affine dodecant_affine(int N, int k);
 Affine sector_affine(int N, int k);
 
-// Planes schedule for N: the n stages of each axis are split into groups of
-// at most 4 and the passes alternate x, y, x, y, ...
-PlanesSchedule make_planes_schedule(int N);
-
 inline int ilog2(int N) {
     int n = 0;
     while ((1 << n) < N) ++n;
@@ -107,24 +86,6 @@ inline int ilog2(int N) {
 }
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-// Per-dodecant pointers of one pass launch.
-struct SlotPtrs {
-    const void* in;
-    void* out;
-    Affine map;
-};
-
-struct PassLaunch {
-    SlotPtrs slot[kMaxSlots];
-    int N, n;
-    int axis, m0;
-    Geo gin, gout;
-    int dmax;             // 3N
-    int V;                // valid outputs per warp tile
-    int ntiles;           // warp tiles along d
-    long long warps;      // warps per slot
-};
 
 // Element type of a buffer read or written by a fused pass.
 enum class ElemKind : int { U8 = 0, I16 = 1, I32 = 2, F32 = 3, U16 = 4 };
@@ -311,9 +272,6 @@ cudaError_t encode_fused_tmap(const FusedLaunch& L, const void* in_base, size_t 
 // pass).  `V` stored positions per tile; tile origins are placed by the kernel.
 void adjoint_fused_tile(int G, int* V, int* PB);
 cudaError_t launch_planes_adjoint_fused(const FusedLaunch& L, int G, bool is_float, int nslots, cudaStream_t s);
-cudaError_t launch_planes_pass(const PassLaunch& L, int G, drt3d_dtype in_dtype, bool ingest,
-                               bool is_float, int nslots, cudaStream_t s);
-cudaError_t launch_planes_adjoint_pass(const PassLaunch& L, int G, bool is_float, int nslots, cudaStream_t s);
 
 }  // namespace drt3d
 
@@ -337,7 +295,6 @@ struct drt3d_plan {
     unsigned flags;
     int device;
     int* d_status;  // device status word (drt3d_status), 0 = OK
-    drt3d::PlanesSchedule planes;  // one-axis passes (adjoint)
     drt3d::FusedSchedule fused;    // two-axis passes (forward)
     // Float32 plans of the coarser sizes N/2, N/4, ..., 2 used by the
     // iterative inverse, indexed by log2 of their size; host-only, created on
