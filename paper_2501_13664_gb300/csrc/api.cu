@@ -677,7 +677,7 @@ drt3d_status drt3d_planes_inverse(const drt3d_plan* P, const int32_t* d_R, int d
         L.in = (i == 0) ? (const void*)d_R : (const void*)(ws + (size_t)((i - 1) & 1) * buf);
         L.out = L.scatter ? (void*)d_vol : (void*)(ws + (size_t)(i & 1) * buf);
         char nm[40];
-        std::snprintf(nm, sizeof nm, "planes_inv_pass %c G=%d m0=%d", t.axis ? 'y' : 'x', t.G, t.m0);
+        std::snprintf(nm, sizeof nm, "planes_inverse %c G=%d m0=%d", t.axis ? 'y' : 'x', t.G, t.m0);
         const double W = 3.0 * N - L.gin.base;
         const double outb = L.scatter ? (double)N * N * N * 4 : (double)N * N * (3.0 * N - L.lo_out) * 4;
         prof_begin(P, stream, nm, (double)N * N * W * 4 + outb);
