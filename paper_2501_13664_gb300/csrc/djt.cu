@@ -108,7 +108,14 @@ djt_pass(const __grid_constant__ DjtLaunch L) {
                   (d2_0 - L.out_base) + p0;
         }
         const bool full = K % 4 == 0 && p0 + K <= vmax && d2_0 + p0 + K <= dmax;
-        if (full) {
+        if (K == 8 && full && (reinterpret_cast<uintptr_t>(dst) & 31u) == 0) {
+            // a lane's eight displacements as one 32-byte store: every sector is
+            // written whole by one instruction
+            asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst), "r"(v[t2][0]),
+                         "r"(v[t2][1 % K]), "r"(v[t2][2 % K]), "r"(v[t2][3 % K]), "r"(v[t2][4 % K]), "r"(v[t2][5 % K]),
+                         "r"(v[t2][6 % K]), "r"(v[t2][7 % K])
+                         : "memory");
+        } else if (full) {
 #pragma unroll
             for (int c = 0; c < K / 4; ++c) {
                 uint4 x = make_uint4(v[t2][4 * c], v[t2][4 * c + 1], v[t2][4 * c + 2], v[t2][4 * c + 3]);
