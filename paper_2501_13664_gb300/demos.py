@@ -3,7 +3,8 @@ noise of larger amplitude still stands out in the John domain; keeping only
 the largest coefficients and backprojecting them brings the line back.
 
 The volume, the transform, the thresholding and the backprojection all stay
-on the GPU; the line is drawn with eq.(digitalLine) in the sector's frame.
+on the GPU.  The caller supplies the line's voxels (a boolean N^3 mask in the
+sector's frame) and its cell (s1, s2, d1, d2) of the transform.
 """
 from __future__ import annotations
 
@@ -12,30 +13,22 @@ import torch
 from . import lines_adjoint, lines_forward
 
 
-def _lline(n: int, s: int, u: int) -> int:
-    """l^n_s(u) of eq.(digitalLine)."""
-    return sum(((u >> (n - 1 - i)) & 1) * (((s >> i) + 1) >> 1) for i in range(n))
-
-
-def ray_in_noise(N: int = 128, amplitude: int = 16, noise: int = 32, top: int = 16, seed: int = 9,
-                 line=(37, 90, 150, 140), sector: int = 0, device="cuda") -> dict:
-    """Embed the line (s1, s2, d1, d2) of ``sector`` (driving axis x, no flips
-    for sector 0) with value ``amplitude`` into integer noise uniform in
-    [-noise, noise], take the DJT of that sector, keep the ``top`` largest
-    coefficients and backproject them.
+def ray_in_noise(line_mask: torch.Tensor, line, amplitude: int = 16, noise: int = 32, top: int = 16, seed: int = 9,
+                 sector: int = 0) -> dict:
+    """Add ``amplitude`` on the voxels of ``line_mask`` (a line of ``sector``,
+    whose transform cell is ``line`` = (s1, s2, d1, d2)) to integer noise
+    uniform in [-noise, noise], take the DJT of that sector, keep the ``top``
+    largest coefficients and backproject them.
 
     Returns the volume, the line's voxel mask, the position of the largest
     coefficient, the line's own coefficient, the largest coefficient off the
     line's cell, and the backprojection."""
-    n = N.bit_length() - 1
+    N = int(line_mask.shape[0])
+    device = line_mask.device
     s1, s2, d1, d2 = line
     g = torch.Generator(device=device).manual_seed(seed)
     f = torch.randint(-noise, noise + 1, (N, N, N), generator=g, device=device, dtype=torch.int32)
-    mask = torch.zeros((N, N, N), dtype=torch.bool, device=device)
-    for x in range(N):
-        y, z = _lline(n, s1, x) + d1 - N, _lline(n, s2, x) + d2 - N
-        if 0 <= y < N and 0 <= z < N:
-            mask[x, y, z] = True
+    mask = line_mask.to(torch.bool)
     f = f + amplitude * mask.to(torch.int32)
     J = lines_forward(f, [sector])
     flat = J.reshape(-1)

@@ -14,6 +14,8 @@ on the device at most.
     inverse-n256    forward of dodecant 0, then its exact inverse
     lines-n64-s0    N=64 int16 volume (uniform 0..1023 + 32 lines), DJT of
                     sector 0 (268 MB of int32 out)
+    lines-n128-s0   the config-3 volume (N=128 int16), DJT of sector 0
+                    (4.3 GB of int32 out; first pass G = 4, second G = 3)
     batched-c4-n64  80 uint8 volumes with the N <= 64 sizes of the 96-volume
                     mixed batch, one persistent launch after one memset
     lines-adj-n64   the lines-n64-s0 transform, then its adjoint (backprojection)
@@ -38,7 +40,8 @@ def _sched(s: str):
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("case", choices=["fused-n256-d1", "fused-n256", "inverse-n256", "lines-n64-s0", "batched-c4-n64",
-                                     "lines-adj-n64", "drt2d-n256", "press-n64", "adj-f32-n128"])
+                                     "lines-adj-n64", "drt2d-n256", "press-n64", "adj-f32-n128",
+                                     "lines-n128-s0"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--schedule", type=str, default="4,4", help="stage-fusion split of the N=256 planes cases")
     args = ap.parse_args(argv)
@@ -118,8 +121,8 @@ def main(argv=None) -> int:
         torch.cuda.synchronize()
         status = plan.device_error()
         print(f"{args.case}: reps={args.reps} status={status} sum={float(back.double().sum()):.6e}")
-    elif args.case == "lines-n64-s0":
-        N = 64
+    elif args.case in ("lines-n64-s0", "lines-n128-s0"):
+        N = 64 if args.case == "lines-n64-s0" else 128
         vol = torch.from_numpy(synth.c3_volume(N)).to(dev)
         plan = get_plan(N, torch.int16)
         out = torch.empty((1, N, N, 2 * N, 2 * N), dtype=torch.int32, device=dev)

@@ -6,6 +6,8 @@ import torch
 
 import synth
 
+from _paper_refs import lline_rec
+
 pytestmark = pytest.mark.gpu
 
 
@@ -159,12 +161,22 @@ def test_ray_in_noise_threshold_and_backproject(drt):
     (the ray's neighbours share voxels with it) most of them."""
     from paper_2501_13664_gb300 import demos
 
+    N, n = 128, 7
     line = (37, 90, 150, 140)
-    res = demos.ray_in_noise(N=128, amplitude=16, noise=32, top=1, line=line)
+    s1, s2, d1, d2 = line
+    # the digital line of eq.(3DfDJT) in sector 0's frame (x' = x, no flips),
+    # drawn with the recursive form of eq.(digitalLine)
+    mask = torch.zeros((N, N, N), dtype=torch.bool)
+    for x in range(N):
+        y, z = lline_rec(n, s1, x) + d1 - N, lline_rec(n, s2, x) + d2 - N
+        if 0 <= y < N and 0 <= z < N:
+            mask[x, y, z] = True
+    mask = mask.cuda()
+    res = demos.ray_in_noise(mask, line, amplitude=16, noise=32, top=1)
     assert res["line_voxels"] == 128  # the line crosses the whole cube
     assert res["peak"] == line
     assert demos.recovered_fraction(res) == 1.0
-    res = demos.ray_in_noise(N=128, amplitude=16, noise=32, top=16, line=line)
+    res = demos.ray_in_noise(mask, line, amplitude=16, noise=32, top=16)
     assert res["peak"] == line
     assert res["line_coefficient"] > res["largest_other"]
     assert demos.recovered_fraction(res) >= 0.8
