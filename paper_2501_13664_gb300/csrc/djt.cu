@@ -69,11 +69,34 @@ djt_pass(const __grid_constant__ DjtLaunch L) {
             const int yp = d1i - N;
             const bool rok = yp >= 0 && yp < N;
             const long long rb = sp.map.o0 + (long long)vv * sp.map.sx + (long long)(rok ? yp : 0) * sp.map.sy;
+            const int z0 = q0 - N;  // z' of the lane's first element
+            if (sp.map.sz == 1 || sp.map.sz == -1) {
+                // z' runs along memory: one row pointer, and no per-element
+                // bounds test for a lane whose K elements all lie inside
+                const TIn* rp = vol + rb + (long long)z0 * sp.map.sz;
+                const bool all_in = rok && z0 >= 0 && z0 + K <= N;
+                if (all_in) {
+                    if (sp.map.sz == 1) {
 #pragma unroll
-            for (int i = 0; i < K; ++i) {
-                const int zp = q0 + i - N;
-                const bool ok = rok && zp >= 0 && zp < N;
-                v[u][i] = ok ? (uint32_t)(int32_t)vol[rb + (long long)zp * sp.map.sz] : 0u;
+                        for (int i = 0; i < K; ++i) v[u][i] = (uint32_t)(int32_t)rp[i];
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < K; ++i) v[u][i] = (uint32_t)(int32_t)rp[-i];
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < K; ++i) {
+                        const bool ok = rok && z0 + i >= 0 && z0 + i < N;
+                        v[u][i] = ok ? (uint32_t)(int32_t)rp[(int)sp.map.sz * i] : 0u;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < K; ++i) {
+                    const int zp = z0 + i;
+                    const bool ok = rok && zp >= 0 && zp < N;
+                    v[u][i] = ok ? (uint32_t)(int32_t)vol[rb + (long long)zp * sp.map.sz] : 0u;
+                }
             }
         } else {
             const uint32_t* in = static_cast<const uint32_t*>(sp.in);
@@ -121,6 +144,9 @@ djt_pass(const __grid_constant__ DjtLaunch L) {
                 uint4 x = make_uint4(v[t2][4 * c], v[t2][4 * c + 1], v[t2][4 * c + 2], v[t2][4 * c + 3]);
                 *reinterpret_cast<uint4*>(dst + 4 * c) = x;
             }
+        } else if (p0 + K <= vmax && d2_0 + p0 + K <= dmax) {
+#pragma unroll
+            for (int i = 0; i < K; ++i) dst[i] = v[t2][i];
         } else {
 #pragma unroll
             for (int i = 0; i < K; ++i)
