@@ -59,6 +59,9 @@ template <int G> __host__ __device__ constexpr int fused_warps() { return G >= 3
 // outputs plus the 2^G - 1 the phase-2 shifts reach past them.
 template <int G> __host__ __device__ constexpr int fused_v() { return (WT - 2 * ((1 << G) - 1)) & ~3; }
 template <int G> __host__ __device__ constexpr int fused_ws() { return (fused_v<G>() + (1 << G) - 1 + 3) & ~3; }
+// Elements after the last phase-1 row that its lanes past WS read (they read
+// on into the next row; for the last row, into this pad).
+template <int G> __host__ __device__ constexpr int fused_pad() { return WT - fused_ws<G>() > K ? WT - fused_ws<G>() : K; }
 
 // Staged (TMA) input of one phase-1 group: 2^G rows of WT + 8 16-bit
 // elements, the window [q, q + WT) of a row rounded out to 8-element (16-byte)
@@ -309,7 +312,7 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
     constexpr int NW = fused_warps<G>();
     constexpr int GPW = R / NW > 0 ? R / NW : 1;  // row groups per warp
     constexpr int WS = fused_ws<G>();
-    TS* S = reinterpret_cast<TS*>(smem_raw);  // [u2][t1][WS] (+ K pad)
+    TS* S = reinterpret_cast<TS*>(smem_raw);  // [u2][t1][WS] (+ pad)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool active = warp < NW;
     const int m0 = L.m0;
@@ -680,7 +683,7 @@ __device__ __forceinline__ void fused_cta_u8x2(const FusedLaunch& L, const Fused
     constexpr int R = 1 << G;
     constexpr int NW = fused_warps<G>();
     constexpr int WS = fused_ws<G>();
-    uint16_t* S = reinterpret_cast<uint16_t*>(smem_raw);  // [u2][t1][WS] (+ K pad)
+    uint16_t* S = reinterpret_cast<uint16_t*>(smem_raw);  // [u2][t1][WS] (+ pad)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = L.N;
     const unsigned ntiles = (unsigned)L.ntiles;

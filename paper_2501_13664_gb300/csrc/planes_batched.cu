@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(256, 2) planes_batched(const __grid_constant__
     }
 }
 
-size_t batched_smem_bytes() { return ((size_t)(1 << 8) * fused_ws<4>() + K) * sizeof(uint32_t) + 128; }
+size_t batched_smem_bytes() { return ((size_t)(1 << 8) * fused_ws<4>() + fused_pad<4>()) * sizeof(uint32_t) + 128; }
 
 }  // namespace
 

@@ -45,7 +45,7 @@ planes_fused(const __grid_constant__ FusedLaunch L) {
 
 template <typename TIn, typename TOut, typename T, typename TS, int G, bool INGEST>
 cudaError_t launch_g(const FusedLaunch& Lin, int nslots, cudaStream_t s) {
-    const size_t smem = ((size_t)(1 << (2 * G)) * fused_ws<G>() + K) * sizeof(TS);
+    const size_t smem = ((size_t)(1 << (2 * G)) * fused_ws<G>() + fused_pad<G>()) * sizeof(TS);
     auto kern = planes_fused<TIn, TOut, T, TS, G, INGEST>;
     static DeviceOnce attr_done;           // per instantiation
     static std::atomic<int> wave[64] = {};  // resident CTAs of the device, written before the flag
@@ -88,7 +88,7 @@ planes_fused_tma(const __grid_constant__ FusedLaunch L, const __grid_constant__ 
 
 template <typename TOut, int G>
 cudaError_t launch_tma_g(const FusedLaunch& L, const CUtensorMap& map, int nslots, cudaStream_t s) {
-    const size_t smem = ((size_t)(1 << (2 * G)) * fused_ws<G>() + K) * 4 + 128;
+    const size_t smem = ((size_t)(1 << (2 * G)) * fused_ws<G>() + fused_pad<G>()) * 4 + 128;
     auto kern = planes_fused_tma<TOut, G>;
     static DeviceOnce attr_done;  // per instantiation
     int dev = 0;
