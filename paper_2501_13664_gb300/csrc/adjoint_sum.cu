@@ -35,6 +35,7 @@ struct Cube {
 template <typename T, int C>
 __global__ void __launch_bounds__(kSumThreads)
 frames_sum_kernel(const __grid_constant__ FramesSum S) {
+    pdl_wait_and_release();
     using Q = Cube<C>;
     __shared__ T cube[Q::WORDS];
     const int N = S.N;
@@ -111,13 +112,12 @@ cudaError_t launch_t(const FramesSum& S, cudaStream_t s) {
     const int nc = S.N / C;
     const unsigned blocks = (unsigned)nc * nc * nc;
     switch (C) {
-    case 2: frames_sum_kernel<T, 2><<<blocks, kSumThreads, 0, s>>>(S); break;
-    case 4: frames_sum_kernel<T, 4><<<blocks, kSumThreads, 0, s>>>(S); break;
-    case 8: frames_sum_kernel<T, 8><<<blocks, kSumThreads, 0, s>>>(S); break;
-    case 16: frames_sum_kernel<T, 16><<<blocks, kSumThreads, 0, s>>>(S); break;
+    case 2: return launch_chained(frames_sum_kernel<T, 2>, dim3(blocks), dim3(kSumThreads), 0, s, S);
+    case 4: return launch_chained(frames_sum_kernel<T, 4>, dim3(blocks), dim3(kSumThreads), 0, s, S);
+    case 8: return launch_chained(frames_sum_kernel<T, 8>, dim3(blocks), dim3(kSumThreads), 0, s, S);
+    case 16: return launch_chained(frames_sum_kernel<T, 16>, dim3(blocks), dim3(kSumThreads), 0, s, S);
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace

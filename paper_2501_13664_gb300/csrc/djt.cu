@@ -40,6 +40,7 @@ __device__ __forceinline__ int lline_dev(int G, int t, int u) {
 template <typename TIn, int G, int K, bool INGEST, bool FINAL>
 __global__ void __launch_bounds__(kDjtWarps * 32)
 djt_pass(const __grid_constant__ DjtLaunch L) {
+    pdl_wait_and_release();
     constexpr int R = 1 << G;
     const int lane = threadIdx.x & 31;
     long long w = (long long)blockIdx.x * kDjtWarps + (threadIdx.x >> 5);
@@ -158,8 +159,8 @@ djt_pass(const __grid_constant__ DjtLaunch L) {
 template <typename TIn, int G, int K, bool INGEST, bool FINAL>
 cudaError_t launch_k(const DjtLaunch& L, int nslots, cudaStream_t s) {
     const long long blocks = (L.warps + kDjtWarps - 1) / kDjtWarps;
-    djt_pass<TIn, G, K, INGEST, FINAL><<<dim3((unsigned)blocks, (unsigned)nslots), kDjtWarps * 32, 0, s>>>(L);
-    return cudaGetLastError();
+    return launch_chained(djt_pass<TIn, G, K, INGEST, FINAL>, dim3((unsigned)blocks, (unsigned)nslots),
+                          dim3(kDjtWarps * 32), 0, s, L);
 }
 
 template <typename TIn, bool INGEST, bool FINAL>

@@ -23,6 +23,7 @@ constexpr int kAdjK = 4;      // displacements per lane
 constexpr int kAdjWarps = 8;
 
 __global__ void __launch_bounds__(kAdjWarps * 32) djt_adj_stage(const __grid_constant__ DjtAdjLaunch L) {
+    pdl_wait_and_release();
     const int lane = threadIdx.x & 31;
     long long w = (long long)blockIdx.x * kAdjWarps + (threadIdx.x >> 5);
     if (w >= L.items) return;
@@ -74,6 +75,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32) djt_adj_stage(const __grid_con
 // sector's driving axis a.  The frame volume is stage 0's row x' at
 // displacements (N + y', N + z') of its window.
 __global__ void __launch_bounds__(256) djt_adj_gather(const __grid_constant__ DjtAdjGather L) {
+    pdl_wait_and_release();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int N = L.N;
     const long long NN = (long long)N * N;
@@ -95,14 +97,12 @@ __global__ void __launch_bounds__(256) djt_adj_gather(const __grid_constant__ Dj
 
 cudaError_t launch_djt_adj_stage(const DjtAdjLaunch& L, int nslots, cudaStream_t s) {
     const long long blocks = (L.items + kAdjWarps - 1) / kAdjWarps;
-    djt_adj_stage<<<dim3((unsigned)blocks, (unsigned)nslots), kAdjWarps * 32, 0, s>>>(L);
-    return cudaGetLastError();
+    return launch_chained(djt_adj_stage, dim3((unsigned)blocks, (unsigned)nslots), dim3(kAdjWarps * 32), 0, s, L);
 }
 
 cudaError_t launch_djt_adj_gather(const DjtAdjGather& L, cudaStream_t s) {
     const long long total = (long long)L.N * L.N * L.N;
-    djt_adj_gather<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(L);
-    return cudaGetLastError();
+    return launch_chained(djt_adj_gather, dim3((unsigned)((total + 255) / 256)), dim3(256), 0, s, L);
 }
 
 int djt_adj_lanes_k() { return kAdjK; }

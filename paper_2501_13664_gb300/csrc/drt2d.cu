@@ -54,6 +54,7 @@ __device__ __forceinline__ void load_run(const TIn* p, TIn (&out)[CNT]) {
 
 template <typename TIn, typename T, int G, bool INGEST>
 __global__ void __launch_bounds__(kWarps2 * 32) drt2d_pass(const __grid_constant__ Drt2dLaunch L) {
+    pdl_wait_and_release();
     constexpr int K = kK2;
     constexpr int R = 1 << G;
     const int lane = threadIdx.x & 31;
@@ -169,13 +170,12 @@ template <typename TIn, typename T, bool INGEST>
 cudaError_t launch_g(const Drt2dLaunch& L, int G, int nslots, cudaStream_t s) {
     const dim3 grid((unsigned)((L.warps + kWarps2 - 1) / kWarps2), (unsigned)nslots);
     switch (G) {
-    case 1: drt2d_pass<TIn, T, 1, INGEST><<<grid, kWarps2 * 32, 0, s>>>(L); break;
-    case 2: drt2d_pass<TIn, T, 2, INGEST><<<grid, kWarps2 * 32, 0, s>>>(L); break;
-    case 3: drt2d_pass<TIn, T, 3, INGEST><<<grid, kWarps2 * 32, 0, s>>>(L); break;
-    case 4: drt2d_pass<TIn, T, 4, INGEST><<<grid, kWarps2 * 32, 0, s>>>(L); break;
+    case 1: return launch_chained(drt2d_pass<TIn, T, 1, INGEST>, grid, dim3(kWarps2 * 32), 0, s, L);
+    case 2: return launch_chained(drt2d_pass<TIn, T, 2, INGEST>, grid, dim3(kWarps2 * 32), 0, s, L);
+    case 3: return launch_chained(drt2d_pass<TIn, T, 3, INGEST>, grid, dim3(kWarps2 * 32), 0, s, L);
+    case 4: return launch_chained(drt2d_pass<TIn, T, 4, INGEST>, grid, dim3(kWarps2 * 32), 0, s, L);
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 // Whole transform of one (image, quadrant) per CTA, for uint8 images with
@@ -186,6 +186,7 @@ cudaError_t launch_g(const Drt2dLaunch& L, int G, int nslots, cudaStream_t s) {
 // tile) pairs of each group, exactly as in drt2d_pass.
 template <int G1, int G2, int NW>
 __global__ void __launch_bounds__(NW * 32, NW >= 16 ? 1 : 2) drt2d_fused(const __grid_constant__ Drt2dLaunch L) {
+    pdl_wait_and_release();
     constexpr int K = kK2;
     constexpr int R1 = 1 << G1, R2 = 1 << G2;
     constexpr int N = R1 * R2, W = 2 * N;
@@ -297,8 +298,7 @@ cudaError_t launch_fused2(const Drt2dLaunch& L, int nslots, cudaStream_t s) {
             attr_done.mark(dev);
         }
     }
-    kern<<<(unsigned)nslots, NW * 32, smem, s>>>(L);
-    return cudaGetLastError();
+    return launch_chained(kern, dim3((unsigned)nslots), dim3(NW * 32), smem, s, L);
 }
 
 }  // namespace

@@ -367,8 +367,11 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
     if constexpr (!INGEST && !TMA && sizeof(TIn) == 4) {
         // Warm L2 with the input rows of the CTA `prefetch_ahead` places later
         // in launch order (about one wave of resident CTAs): one sheared row
-        // window per thread; a hint only.
-        if (L.prefetch_ahead > 0 && threadIdx.x < R * R && (L.gin.pitch & 3) == 0 && (L.gin.base & 3) == 0) {
+        // window per thread, in 16-byte units; a hint only.  A zero tile is
+        // not prefetched.
+        constexpr int EA = 16 / (int)sizeof(TIn);  // elements per 16 bytes
+        if (L.prefetch_ahead > 0 && threadIdx.x < R * R && L.gin.pitch % EA == 0 && L.gin.base % EA == 0 &&
+            L.dmax % EA == 0) {
             const unsigned long long nxt =
                 (unsigned long long)blockIdx.y * gridDim.x + blockIdx.x + (unsigned)L.prefetch_ahead;
             const unsigned ny = (unsigned)(nxt / gridDim.x), nc = (unsigned)(nxt % gridDim.x);
@@ -380,17 +383,21 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
                 const int nsg2 = (int)(nu & ((1u << m0) - 1)); nu >>= m0;
                 const int nwq2 = (int)nu;
                 const int nd0 = L.gout.base + ntile * L.V;
-                const int u1 = threadIdx.x % R, u2 = threadIdx.x / R;
-                const int q = nd0 + nsg2 * u2 + nsg1 * u1;
-                const int lo = max(q & ~3, L.gin.base), hi = min(q + WT + 4, L.dmax);
-                const FusedSlot& ns = L.slot[ny];
-                const bool nswap = ns.swap != 0;
-                const int nrs1 = nswap ? 1 : N, nrs2 = nswap ? N : 1;
-                const long long row = (long long)(nsg1 + (u1 << m0) + (nwq1 << (m0 + G))) * nrs1 +
-                                      (long long)(nsg2 + (u2 << m0) + (nwq2 << (m0 + G))) * nrs2;
-                if (lo < hi)
-                    tma::prefetch_l2(static_cast<const TIn*>(ns.in) + row * L.gin.pitch + (lo - L.gin.base),
-                                     (uint32_t)(hi - lo) * 4u);
+                const int nsmax = (nsg1 << G) + (nsg2 << G) + 2 * (R - 1);
+                if (nd0 + L.V > 2 * N - nsmax) {
+                    const int u1 = threadIdx.x % R, u2 = threadIdx.x / R;
+                    const int q = nd0 + nsg2 * u2 + nsg1 * u1;
+                    // the loads read [q rounded down to 16 bytes, + WT + 16 bytes)
+                    const int lo = max(q & ~(EA - 1), L.gin.base), hi = min(lo + WT + 2 * EA, L.dmax);
+                    const FusedSlot& ns = L.slot[ny];
+                    const bool nswap = ns.swap != 0;
+                    const int nrs1 = nswap ? 1 : N, nrs2 = nswap ? N : 1;
+                    const long long row = (long long)(nsg1 + (u1 << m0) + (nwq1 << (m0 + G))) * nrs1 +
+                                          (long long)(nsg2 + (u2 << m0) + (nwq2 << (m0 + G))) * nrs2;
+                    if (lo < hi)
+                        tma::prefetch_l2(static_cast<const TIn*>(ns.in) + row * L.gin.pitch + (lo - L.gin.base),
+                                         (uint32_t)(hi - lo) * (uint32_t)sizeof(TIn));
+                }
             }
         }
     }

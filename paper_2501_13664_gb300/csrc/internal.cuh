@@ -35,6 +35,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <utility>
 
 #include "drt3d.h"
 
@@ -58,6 +59,34 @@ struct DeviceOnce {
 inline bool device_is_current(int device) {
     int cur = -1;
     return cudaGetDevice(&cur) == cudaSuccess && cur == device;
+}
+
+// Programmatic dependent launch.  A kernel of a pass chain is launched with
+// programmatic stream serialisation: it may be scheduled while the previous
+// kernel of the stream is still running its last CTAs, and it waits for that
+// kernel's completion (and its memory) before it touches global memory.
+// Each kernel of the chain lets its own dependents launch as soon as all of
+// its CTAs have started.  Both instructions are no-ops for kernels launched
+// the ordinary way.
+__device__ __forceinline__ void pdl_wait_and_release() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chained(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                           Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
 constexpr int kMaxSlots = 12;

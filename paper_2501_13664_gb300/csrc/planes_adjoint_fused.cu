@@ -80,6 +80,7 @@ __device__ __forceinline__ AdjTile adj_tile(const FusedLaunch& L, unsigned x) {
 template <typename T, int G>
 __global__ void __launch_bounds__(32 * fused_warps<G>(), (G >= 4 ? 2 : 1))
 planes_adj_fused(const __grid_constant__ FusedLaunch L) {
+    pdl_wait_and_release();
     constexpr int R = 1 << G;
     constexpr int NW = fused_warps<G>();
     constexpr int GPW = R / NW > 0 ? R / NW : 1;  // row groups per warp
@@ -231,8 +232,7 @@ cudaError_t launch_adj_g(const FusedLaunch& Lin, int nslots, cudaStream_t s) {
     FusedLaunch L = Lin;
     L.prefetch_ahead = wave[dev].load(std::memory_order_relaxed);  // one wave ahead
     dim3 grid((unsigned)L.ctas, (unsigned)nslots);
-    kern<<<grid, 32 * fused_warps<G>(), smem, s>>>(L);
-    return cudaGetLastError();
+    return launch_chained(kern, grid, dim3(32 * fused_warps<G>()), smem, s, L);
 }
 
 template <typename T>

@@ -33,6 +33,7 @@ template <typename TIn, typename TOut, typename T, typename TS, int G, bool INGE
 __global__ void __launch_bounds__(32 * fused_warps<G>(), (G >= 4 ? 2 : 1))
 planes_fused(const __grid_constant__ FusedLaunch L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_wait_and_release();
     if constexpr (INGEST && G == 4 && std::is_same<TIn, uint8_t>::value && std::is_same<TS, uint16_t>::value) {
         if (!L.global_layout && !L.slot[blockIdx.y].sub)  // 16-bit sums: two groups per register
             fused_cta_u8x2<TOut, G>(L, L.slot[blockIdx.y], blockIdx.x, smem_raw);
@@ -68,8 +69,7 @@ cudaError_t launch_g(const FusedLaunch& Lin, int nslots, cudaStream_t s) {
     // 32-bit buffer input read by the register loader: prefetch one wave ahead
     L.prefetch_ahead = (!INGEST && sizeof(TIn) == 4) ? wave[dev].load(std::memory_order_relaxed) : 0;
     dim3 grid((unsigned)L.ctas, (unsigned)nslots);
-    kern<<<grid, 32 * fused_warps<G>(), smem, s>>>(L);
-    return cudaGetLastError();
+    return launch_chained(kern, grid, dim3(32 * fused_warps<G>()), smem, s, L);
 }
 
 // Pass over 16-bit buffer rows with the phase-1 input staged by TMA: one
@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(32 * fused_warps<G>(), (G >= 4 ? 2 : 1))
 planes_fused_tma(const __grid_constant__ FusedLaunch L, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar[1 << G];
+    pdl_wait_and_release();
     // TMA destinations are kept 128-byte aligned.
     unsigned char* sm = smem_raw + ((128u - (tma::smem_u32(smem_raw) & 127u)) & 127u);
     fused_cta<uint16_t, TOut, uint32_t, uint32_t, G, false, false, true>(L, L.slot[blockIdx.y], blockIdx.x, sm,
@@ -99,8 +100,7 @@ cudaError_t launch_tma_g(const FusedLaunch& L, const CUtensorMap& map, int nslot
         attr_done.mark(dev);
     }
     dim3 grid((unsigned)L.ctas, (unsigned)nslots);
-    kern<<<grid, 32 * fused_warps<G>(), smem, s>>>(L, map);
-    return cudaGetLastError();
+    return launch_chained(kern, grid, dim3(32 * fused_warps<G>()), smem, s, L, map);
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,

@@ -199,6 +199,7 @@ __device__ __forceinline__ void stage_pair(uint32_t* s0, uint32_t* s1, int off0,
 template <int G, int CH, bool MULTI>
 __global__ void __launch_bounds__(inv_warps(G) * 32, (G >= 4 ? (CH <= 8 ? 4 : CH <= 16 ? 3 : 2) : 4))
 planes_inv_pass(const __grid_constant__ InvLaunch L) {
+    pdl_wait_and_release();
     constexpr int R = 1 << G;
     constexpr int NW = inv_warps(G);
     constexpr int NT = NW * 32;
@@ -629,6 +630,7 @@ __device__ __forceinline__ void inv_stages(const InvLaunch& L, const InvCtx& C, 
 template <int G, int VPL>
 __global__ void __launch_bounds__(inv_warps(G) * 32, (G >= 4 ? (VPL >= 7 ? 3 : 4) : (VPL >= 7 ? 5 : 8)))
 planes_inv_group(const __grid_constant__ InvLaunch L) {
+    pdl_wait_and_release();
     constexpr int R = 1 << G;
     constexpr int NW = inv_warps(G);
     constexpr int CH = 4 * VPL;
@@ -766,8 +768,7 @@ cudaError_t launch_inv_group(const InvLaunch& L, cudaStream_t s) {
         attr_done.mark(dev);
     }
     const unsigned units = (unsigned)((long long)L.N << (L.n - G));
-    kern<<<units, inv_warps(G) * 32, smem, s>>>(L);
-    return cudaGetLastError();
+    return launch_chained(kern, dim3(units), dim3(inv_warps(G) * 32), smem, s, L);
 }
 
 template <int G>
@@ -812,8 +813,7 @@ cudaError_t launch_inv_gc(const InvLaunch& L, cudaStream_t s) {
     }
     if (smem > (size_t)optin_max[dev].load(std::memory_order_relaxed)) return cudaErrorInvalidValue;
     const unsigned units = (unsigned)((long long)L.N << (L.n - G));
-    kern<<<units, inv_warps(G) * 32, smem, s>>>(L);
-    return cudaGetLastError();
+    return launch_chained(kern, dim3(units), dim3(inv_warps(G) * 32), smem, s, L);
 }
 
 template <int G>

@@ -23,6 +23,7 @@ constexpr int kThreads = 256;
 template <bool ACC>
 __global__ void __launch_bounds__(kThreads) press_filter(const float* __restrict__ b, float* __restrict__ y, int N,
                                                          float c) {
+    pdl_wait_and_release();
     const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
     const long long NN = (long long)N * N;
     if (i >= NN * N) return;
@@ -49,6 +50,7 @@ __global__ void __launch_bounds__(kThreads) press_filter(const float* __restrict
 
 // Fine voxel (i, j, k) <- coarse voxel (i/2, j/2, k/2); N is the fine size.
 __global__ void __launch_bounds__(kThreads) press_prolong(const float* __restrict__ xc, float* __restrict__ x, int N) {
+    pdl_wait_and_release();
     const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
     const long long NN = (long long)N * N;
     if (i >= NN * N) return;
@@ -61,6 +63,7 @@ __global__ void __launch_bounds__(kThreads) press_prolong(const float* __restric
 // d in [0, 3Nc); R has pitch 3N = 6Nc.
 __global__ void __launch_bounds__(kThreads) press_restrict(const float* __restrict__ R, float* __restrict__ Rc,
                                                            int Nc) {
+    pdl_wait_and_release();
     const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
     const int Wc = 3 * Nc, W = 6 * Nc, N = 2 * Nc;
     const long long per = (long long)Nc * Nc * Wc;
@@ -76,6 +79,7 @@ __global__ void __launch_bounds__(kThreads) press_restrict(const float* __restri
 // Exact solve at N = 1: the voxel is at d = 2 of each dodecant's column;
 // average the twelve values in dodecant order.
 __global__ void press_coarsest(const float* __restrict__ R1, float* __restrict__ x1) {
+    pdl_wait_and_release();
     float s = 0.f;
     for (int k = 0; k < 12; ++k) s += R1[k * 3 + 2];
     x1[0] = s / 12.f;
@@ -84,6 +88,7 @@ __global__ void press_coarsest(const float* __restrict__ R1, float* __restrict__
 // t = r - t (t holds A x on entry).
 __global__ void __launch_bounds__(kThreads) press_residual(const float* __restrict__ r, float* __restrict__ t,
                                                            long long n) {
+    pdl_wait_and_release();
     const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
     if (i < n) t[i] = __ldg(r + i) - t[i];
 }
@@ -91,6 +96,7 @@ __global__ void __launch_bounds__(kThreads) press_residual(const float* __restri
 // y += x.
 __global__ void __launch_bounds__(kThreads) press_add(const float* __restrict__ x, float* __restrict__ y,
                                                       long long n) {
+    pdl_wait_and_release();
     const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
     if (i < n) y[i] += __ldg(x + i);
 }
@@ -99,6 +105,7 @@ __global__ void __launch_bounds__(kThreads) press_add(const float* __restrict__ 
 // contiguous range, so the total does not depend on scheduling.
 __global__ void __launch_bounds__(kThreads) press_sumsq(const float* __restrict__ y, long long n, long long chunk,
                                                         double* __restrict__ partial) {
+    pdl_wait_and_release();
     __shared__ double red[kThreads];
     const long long lo = (long long)blockIdx.x * chunk;
     const long long hi = min(n, lo + chunk);
@@ -121,6 +128,7 @@ __global__ void __launch_bounds__(kThreads) press_sumsq(const float* __restrict_
 __global__ void __launch_bounds__(kThreads) press_normalize(const float* __restrict__ y, float* __restrict__ x,
                                                             long long n, const double* __restrict__ partial,
                                                             int nparts, double* __restrict__ norm) {
+    pdl_wait_and_release();
     __shared__ float inv;
     if (threadIdx.x == 0) {
         double t = 0.0;
@@ -140,45 +148,37 @@ unsigned blocks_for(long long n) { return (unsigned)((n + kThreads - 1) / kThrea
 
 cudaError_t launch_press_filter(const float* b, float* y, int N, float c, bool accumulate, cudaStream_t s) {
     const long long n = (long long)N * N * N;
-    if (accumulate)
-        press_filter<true><<<blocks_for(n), kThreads, 0, s>>>(b, y, N, c);
-    else
-        press_filter<false><<<blocks_for(n), kThreads, 0, s>>>(b, y, N, c);
-    return cudaGetLastError();
+    if (accumulate) return launch_chained(press_filter<true>, dim3(blocks_for(n)), dim3(kThreads), 0, s, b, y, N, c);
+    return launch_chained(press_filter<false>, dim3(blocks_for(n)), dim3(kThreads), 0, s, b, y, N, c);
 }
 
 cudaError_t launch_press_prolong(const float* xc, float* x, int N, cudaStream_t s) {
-    press_prolong<<<blocks_for((long long)N * N * N), kThreads, 0, s>>>(xc, x, N);
-    return cudaGetLastError();
+    return launch_chained(press_prolong, dim3(blocks_for((long long)N * N * N)), dim3(kThreads), 0, s, xc, x, N);
 }
 
 cudaError_t launch_press_restrict(const float* R, float* Rc, int Nc, cudaStream_t s) {
-    press_restrict<<<blocks_for(12LL * Nc * Nc * 3 * Nc), kThreads, 0, s>>>(R, Rc, Nc);
-    return cudaGetLastError();
+    return launch_chained(press_restrict, dim3(blocks_for(12LL * Nc * Nc * 3 * Nc)), dim3(kThreads), 0, s, R, Rc, Nc);
 }
 
 cudaError_t launch_press_coarsest(const float* R1, float* x1, cudaStream_t s) {
-    press_coarsest<<<1, 1, 0, s>>>(R1, x1);
-    return cudaGetLastError();
+    return launch_chained(press_coarsest, dim3(1), dim3(1), 0, s, R1, x1);
 }
 
 cudaError_t launch_press_residual(const float* r, float* t, long long n, cudaStream_t s) {
-    press_residual<<<blocks_for(n), kThreads, 0, s>>>(r, t, n);
-    return cudaGetLastError();
+    return launch_chained(press_residual, dim3(blocks_for(n)), dim3(kThreads), 0, s, r, t, n);
 }
 
 cudaError_t launch_press_add(const float* x, float* y, long long n, cudaStream_t s) {
-    press_add<<<blocks_for(n), kThreads, 0, s>>>(x, y, n);
-    return cudaGetLastError();
+    return launch_chained(press_add, dim3(blocks_for(n)), dim3(kThreads), 0, s, x, y, n);
 }
 
 cudaError_t launch_press_normalize(const float* y, float* x, long long n, double* partial, double* norm,
                                    cudaStream_t s) {
     const long long chunk = (n + kPressNormParts - 1) / kPressNormParts;
-    press_sumsq<<<kPressNormParts, kThreads, 0, s>>>(y, n, chunk, partial);
+    const cudaError_t e = launch_chained(press_sumsq, dim3(kPressNormParts), dim3(kThreads), 0, s, y, n, chunk, partial);
+    if (e != cudaSuccess) return e;
     const unsigned nb = (unsigned)std::min<long long>(blocks_for(n), 4096);
-    press_normalize<<<nb, kThreads, 0, s>>>(y, x, n, partial, kPressNormParts, norm);
-    return cudaGetLastError();
+    return launch_chained(press_normalize, dim3(nb), dim3(kThreads), 0, s, y, x, n, partial, kPressNormParts, norm);
 }
 
 }  // namespace drt3d

@@ -11,6 +11,7 @@ namespace {
 template <typename T>
 __global__ void __launch_bounds__(256) transpose_tile32(const T* __restrict__ in, T* __restrict__ out, long long R,
                                                         int C, long long tilesC) {
+    pdl_wait_and_release();
     __shared__ T tile[32][33];
     const long long b = blockIdx.x;
     const long long r0 = (b / tilesC) * 32;
@@ -40,6 +41,7 @@ constexpr int kPitch8 = 80;  // bytes per shared tile row (16-byte aligned)
 
 __global__ void __launch_bounds__(256) transpose_u8_tile64(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
                                                            long long R, long long C, long long tilesC) {
+    pdl_wait_and_release();
     __shared__ __align__(16) uint8_t tile[64 * kPitch8];
     const long long b = blockIdx.x;
     const long long r0 = (b / tilesC) * 64;
@@ -67,29 +69,24 @@ __global__ void __launch_bounds__(256) transpose_u8_tile64(const uint8_t* __rest
 cudaError_t launch_transpose2d(const void* in, void* out, long long R, int C, int esz, cudaStream_t s) {
     if (esz == 1 && R % 64 == 0 && C % 64 == 0) {
         const long long tilesC = C / 64;
-        transpose_u8_tile64<<<(unsigned)((R / 64) * tilesC), 256, 0, s>>>(static_cast<const uint8_t*>(in),
-                                                                          static_cast<uint8_t*>(out), R, C, tilesC);
-        return cudaGetLastError();
+        return launch_chained(transpose_u8_tile64, dim3((unsigned)((R / 64) * tilesC)), dim3(256), 0, s,
+                              static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out), R, C, tilesC);
     }
     const long long tilesC = (C + 31) / 32;
-    const long long blocks = ((R + 31) / 32) * tilesC;
+    const dim3 grid((unsigned)(((R + 31) / 32) * tilesC));
     switch (esz) {
     case 1:
-        transpose_tile32<uint8_t><<<(unsigned)blocks, 256, 0, s>>>(static_cast<const uint8_t*>(in),
-                                                                   static_cast<uint8_t*>(out), R, C, tilesC);
-        break;
+        return launch_chained(transpose_tile32<uint8_t>, grid, dim3(256), 0, s, static_cast<const uint8_t*>(in),
+                              static_cast<uint8_t*>(out), R, C, tilesC);
     case 2:
-        transpose_tile32<uint16_t><<<(unsigned)blocks, 256, 0, s>>>(static_cast<const uint16_t*>(in),
-                                                                    static_cast<uint16_t*>(out), R, C, tilesC);
-        break;
+        return launch_chained(transpose_tile32<uint16_t>, grid, dim3(256), 0, s, static_cast<const uint16_t*>(in),
+                              static_cast<uint16_t*>(out), R, C, tilesC);
     case 4:
-        transpose_tile32<uint32_t><<<(unsigned)blocks, 256, 0, s>>>(static_cast<const uint32_t*>(in),
-                                                                    static_cast<uint32_t*>(out), R, C, tilesC);
-        break;
+        return launch_chained(transpose_tile32<uint32_t>, grid, dim3(256), 0, s, static_cast<const uint32_t*>(in),
+                              static_cast<uint32_t*>(out), R, C, tilesC);
     default:
         return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace drt3d
