@@ -580,11 +580,13 @@ def bench_batched(drt3d, synth, dev, tuned) -> dict:
     vols = [torch.from_numpy(v).to(dev) for v in synth.c4_batch(sizes=sizes)]
     sched = {N: tuple(tuned[N]) for N in set(sizes) if N in tuned}
     bsched = sched
+    btiles = None
     if tuned:
         from paper_2501_13664_gb300 import autotune
 
         bsched = autotune.tune_batched(sizes)  # splits for the persistent kernel's footprint
-    bp = drt3d.BatchPlan(sizes, schedules=bsched)
+        btiles = autotune.tune_batched_items(sizes, bsched)  # work-item size per pass
+    bp = drt3d.BatchPlan(sizes, schedules=bsched, item_tiles=btiles)
     outs = bp.bind(vols)
     plans, wss = {}, {}
     for N in set(sizes):
@@ -640,6 +642,8 @@ def bench_batched(drt3d, synth, dev, tuned) -> dict:
             "speedup": t1 / best, "floor_gbs_batched": floor / (best / 1000) / 1e9,
             "launches_persistent": 1, "launches_one_by_one": sum(len(plans[N].schedule()) for N in sizes),
             "schedules_persistent": {str(N): list(v) for N, v in sorted(bsched.items())},
+            "item_tiles_persistent": ({str(N): list(v) for N, v in sorted(btiles.items())} if btiles
+                                      else "library defaults"),
             "schedules_one_by_one": {str(N): list(v) for N, v in sorted(sched.items())},
             "note": "persistent = one memset + one persistent kernel; multistream = the volumes' per-pass launches "
                     "over k internal streams; both replayed from a CUDA graph; one-by-one = 96 calls on one "

@@ -311,7 +311,8 @@ drt3d_status drt3d_plan_get_schedule(const drt3d_plan* plan, int* ngroups, int G
  * device counter, with a bounded wait (default 2 s) after which the launch
  * records DRT3D_ERR_TIMEOUT and skips the remaining dependent work.
  *   1. drt3d_batch_plan_create(&bp, count, Ns, DRT3D_U8, 0)
- *   2. optionally drt3d_batch_set_schedule(bp, N, ngroups, G) per size
+ *   2. optionally drt3d_batch_set_schedule(bp, N, ngroups, G) and
+ *      drt3d_batch_set_item_tiles(bp, N, npass, tiles) per size
  *   3. drt3d_batch_workspace_bytes(bp, &bytes); allocate it
  *   4. drt3d_batch_bind(bp, descs, d_ws, bytes): uploads the work tables
  *      (allocates small device tables; not for capture)
@@ -332,6 +333,17 @@ drt3d_status drt3d_batch_plan_create(drt3d_batch_plan** plan, int count, const i
                                      unsigned flags);
 drt3d_status drt3d_batch_plan_destroy(drt3d_batch_plan* plan);
 drt3d_status drt3d_batch_set_schedule(drt3d_batch_plan* plan, int N, int ngroups, const int* G);
+/* Work-item size of the persistent launch (mode 0) for the batch's volumes of
+ * size N: tiles[p] consecutive unit-tiles of pass p per claimed item (a unit
+ * is one 2^G x 2^G row block of a fused pass, processed over its displacement
+ * tiles one after another; units follow each other in row-major order); 0
+ * keeps the default (8 tiles at G = 4, whole units grouped to at least 256
+ * rows below).  npass = the number of passes of N's batched schedule; a later
+ * drt3d_batch_set_schedule for N clears the setting.  Not a paper quantity: a
+ * scheduling parameter for the autotuner.  Takes effect at the next bind.
+ * Errors: INVALID_ARG (null, npass mismatch, negative entry), SIZE (no volume
+ * of size N in the batch). */
+drt3d_status drt3d_batch_set_item_tiles(drt3d_batch_plan* plan, int N, int npass, const int* tiles);
 drt3d_status drt3d_batch_workspace_bytes(const drt3d_batch_plan* plan, size_t* bytes);
 drt3d_status drt3d_batch_bind(drt3d_batch_plan* plan, const drt3d_vol_desc* descs, void* d_ws, size_t ws_bytes);
 /* How drt3d_planes_forward_batched runs the bound batch.

@@ -129,7 +129,8 @@ class BatchPlan:
     ``set_mode(1)`` the volumes' per-pass launches over internal streams.
     """
 
-    def __init__(self, Ns, dtype: torch.dtype = torch.uint8, schedules: dict | None = None):
+    def __init__(self, Ns, dtype: torch.dtype = torch.uint8, schedules: dict | None = None,
+                 item_tiles: dict | None = None):
         if dtype != torch.uint8:
             raise TypeError("the batched forward takes uint8 volumes")
         self.Ns = [int(n) for n in Ns]
@@ -143,7 +144,17 @@ class BatchPlan:
             g = (ctypes.c_int * len(groups))(*[int(x) for x in groups])
             _abi.check(self._lib.drt3d_batch_set_schedule(self.handle, int(N), len(groups), g),
                        "drt3d_batch_set_schedule")
+        for N, tiles in (item_tiles or {}).items():
+            self.set_item_tiles(N, tiles)
         self._keep = None
+
+    def set_item_tiles(self, N: int, tiles) -> None:
+        """Unit-tiles per work item of each pass of the persistent launch for
+        the volumes of size N (0 = default); see drt3d_batch_set_item_tiles.
+        Rebind afterwards."""
+        t = (ctypes.c_int * len(tiles))(*[int(x) for x in tiles])
+        _abi.check(self._lib.drt3d_batch_set_item_tiles(self.handle, int(N), len(tiles), t),
+                   "drt3d_batch_set_item_tiles")
 
     def workspace_bytes(self) -> int:
         v = ctypes.c_size_t()

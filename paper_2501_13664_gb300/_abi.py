@@ -51,6 +51,7 @@ SIGNATURES = {
     "drt3d_batch_plan_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(I), I, ctypes.c_uint]),
     "drt3d_batch_plan_destroy": (I, [P]),
     "drt3d_batch_set_schedule": (I, [P, I, I, ctypes.POINTER(I)]),
+    "drt3d_batch_set_item_tiles": (I, [P, I, I, ctypes.POINTER(I)]),
     "drt3d_batch_workspace_bytes": (I, [P, ctypes.POINTER(SZ)]),
     "drt3d_batch_bind": (I, [P, P, P, SZ]),
     "drt3d_planes_forward_batched": (I, [P, P]),

@@ -106,16 +106,18 @@ def tune(Ns, dtype: torch.dtype = torch.uint8, use_cache: bool = True, seed: int
 
 
 def time_batched(N: int, groups, count: int, dtype: torch.dtype = torch.uint8, reps: int = 5,
-                 seed: int = 11) -> float:
+                 seed: int = 11, item_tiles=None) -> float:
     """Median milliseconds of one batched launch of ``count`` volumes of size N
     under ``groups`` (the persistent kernel has one fixed footprint, so the
-    best split can differ from the per-pass launches')."""
+    best split can differ from the per-pass launches'), with ``item_tiles``
+    unit-tiles per work item of each pass (None: the defaults)."""
     from . import BatchPlan
 
     g = torch.Generator(device="cpu").manual_seed(seed)
     vols = [torch.randint(0, 256, (N, N, N), generator=g, dtype=torch.int32).to(dtype).cuda()
             for _ in range(count)]
-    bp = BatchPlan([N] * count, dtype=dtype, schedules={N: tuple(groups)})
+    bp = BatchPlan([N] * count, dtype=dtype, schedules={N: tuple(groups)},
+                   item_tiles={N: list(item_tiles)} if item_tiles is not None else None)
     bp.bind(vols)
     for _ in range(2):
         bp.run()
@@ -155,3 +157,43 @@ def tune_batched(sizes, dtype: torch.dtype = torch.uint8, use_cache: bool = True
         save_cache(cache)
     return best
 
+
+# Work-item sizes tried for each pass of the persistent launch (unit-tiles per
+# item; 0 = the library's default).
+ITEM_TILES = (0, 2, 4, 8, 16, 32, 64)
+
+
+def tune_batched_items(sizes, schedules: dict, dtype: torch.dtype = torch.uint8, use_cache: bool = True,
+                       max_count: int = 4) -> dict:
+    """{N: unit-tiles per work item of each pass} for the persistent launch:
+    one sweep over the passes, each pass's candidates timed with the other
+    passes at their best so far, on up to ``max_count`` volumes of size N
+    alone under ``schedules[N]``."""
+    cache = load_cache() if use_cache else {}
+    best = {}
+    counts = {}
+    for n in sizes:
+        counts[int(n)] = counts.get(int(n), 0) + 1
+    for N in sorted(counts):
+        groups = tuple(schedules[N])
+        key = "batched_items|" + _key(N, dtype) + "|" + ",".join(str(g) for g in groups)
+        if key in cache:
+            best[N] = list(cache[key]["item_tiles"])
+            continue
+        c = min(counts[N], max_count)
+        tiles = [0] * len(groups)
+        ms = {}
+        for p in range(len(groups)):
+            res = {}
+            for cand in ITEM_TILES:
+                t = list(tiles)
+                t[p] = cand
+                res[cand] = time_batched(N, groups, c, dtype, item_tiles=t)
+            tiles[p] = min(res, key=res.get)
+            ms[str(p)] = {str(k): v for k, v in res.items()}
+        best[N] = tiles
+        cache[key] = {"item_tiles": tiles, "ms": ms, "count": c}
+        torch.cuda.empty_cache()
+    if use_cache:
+        save_cache(cache)
+    return best

@@ -300,8 +300,11 @@ __device__ __forceinline__ void store_rows(const FusedLaunch& L, const FusedSlot
 // the block must call it (it synchronises); warps at or past fused_warps<G>()
 // idle.  With COHERENT the input is read with plain loads instead of the
 // read-only path (the batched kernel reads buffers other CTAs of the same
-// launch wrote).
-template <typename TIn, typename TOut, typename T, typename TS, int G, bool INGEST, bool COHERENT, bool TMA = false>
+// launch wrote).  PF compiles the launch-order L2 prefetch in (it reads
+// L.slot at a run-time index; a caller that keeps L in registers leaves it
+// out).
+template <typename TIn, typename TOut, typename T, typename TS, int G, bool INGEST, bool COHERENT, bool TMA = false,
+          bool PF = true>
 __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot& sp, unsigned cta,
                                           unsigned char* smem_raw, const CUtensorMap* tmap = nullptr,
                                           int slot_z = 0, uint64_t* mbar = nullptr) {
@@ -364,7 +367,7 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
         return;
     }
 
-    if constexpr (!INGEST && !TMA && sizeof(TIn) == 4) {
+    if constexpr (PF && !INGEST && !TMA && sizeof(TIn) == 4) {
         // Warm L2 with the input rows of the CTA `prefetch_ahead` places later
         // in launch order (about one wave of resident CTAs): one sheared row
         // window per thread, in 16-byte units; a hint only.  A zero tile is

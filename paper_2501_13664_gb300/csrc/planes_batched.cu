@@ -1,11 +1,13 @@
 // planes_batched.cu -- the planes forward transform of many volumes of
 // different sizes in one persistent launch.
 //
-// Work items are the units of every fused pass of every volume and dodecant
-// (see planes_fused.cu), each with all its displacement tiles.  They are
-// numbered pass-major: all first-pass items of all volumes, then all
-// second-pass items, ...; within a (pass, volume) segment item i is dodecant
-// slot i / units, unit i % units.  Resident
+// Work items are runs of consecutive unit-tiles (a unit of a fused pass, see
+// planes_fused.cu, with one of its displacement tiles; a unit's tiles are
+// consecutive) of every fused pass of every volume and dodecant; the run
+// length is a per-(size, pass) setting (drt3d_batch_set_item_tiles).  Items
+// are numbered pass-major: all first-pass items of all volumes, then all
+// second-pass items, ...; within a (pass, volume) segment item i belongs to
+// dodecant slot i / (items per slot).  Resident
 // CTAs (two per SM) take items from an atomic counter.  An item of pass p > 0
 // reads the intermediate written by every pass p-1 item of its (volume,
 // dodecant); those items were all handed out before it, to CTAs that are
@@ -18,6 +20,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <vector>
 
@@ -36,8 +39,8 @@ struct BatchVol {
     int G[kBatchMaxPass];
     int in_kind[kBatchMaxPass], out_kind[kBatchMaxPass];
     unsigned ctas[kBatchMaxPass];  // items per dodecant slot
-    unsigned upi[kBatchMaxPass];   // units per item (each unit with all its tiles)
-    unsigned units[kBatchMaxPass]; // units per dodecant slot
+    unsigned tpi[kBatchMaxPass];   // unit-tiles per item (consecutive in unit-major order)
+    unsigned cps[kBatchMaxPass];   // unit-tiles per dodecant slot
 };
 
 struct BatchArgs {
@@ -87,7 +90,7 @@ __device__ bool wait_counter(const BatchArgs& A, const unsigned* ctr, unsigned t
 // through a global pointer, the compiler would have to reload them after every
 // store (it cannot prove the output buffers do not alias the tables).
 template <typename TIn, typename TOut, typename TS, int G, bool INGEST, bool TMA = false>
-__device__ __forceinline__ void run_g(const FusedLaunch& Lg, int slot, unsigned item, unsigned upi, unsigned units,
+__device__ __forceinline__ void run_g(const FusedLaunch& Lg, int slot, unsigned item, unsigned tpi, unsigned cps,
                                       unsigned char* smem, const CUtensorMap* tmap = nullptr,
                                       uint64_t* mbar = nullptr, int* status = nullptr) {
     FusedLaunch L;
@@ -101,13 +104,12 @@ __device__ __forceinline__ void run_g(const FusedLaunch& Lg, int slot, unsigned 
     L.ntiles = Lg.ntiles;
     L.ctas = Lg.ctas;
     L.vec_store = Lg.vec_store;
-    L.prefetch_ahead = 0;  // launch order is not item order here
+    L.prefetch_ahead = 0;  // launch order is not item order here (and the prefetch is compiled out)
     L.status = status;
     L.global_layout = 0;
     const FusedSlot sp = Lg.slot[slot];
-    // one item = `upi` consecutive units, each with all its displacement tiles
-    const unsigned nt = (unsigned)L.ntiles;
-    const unsigned c0 = item * upi * nt, c1 = min(item * upi + upi, units) * nt;
+    // one item = `tpi` consecutive unit-tiles (unit-major: a unit's tiles are consecutive)
+    const unsigned c0 = item * tpi, c1 = min(c0 + tpi, cps);
     // The staged rows were written by other CTAs through the generic proxy
     // (made visible to this one by the dependency wait): one proxy fence per
     // thread orders them before all of this item's TMA reads.
@@ -115,21 +117,21 @@ __device__ __forceinline__ void run_g(const FusedLaunch& Lg, int slot, unsigned 
     for (unsigned c = c0; c < c1; ++c) {
         if (c > c0) __syncthreads();  // the previous tile's phase 2 is done with shared memory
         if constexpr (TMA)
-            fused_cta<TIn, TOut, uint32_t, TS, G, false, false, true>(L, sp, c, smem, tmap, slot, mbar);
+            fused_cta<TIn, TOut, uint32_t, TS, G, false, false, true, false>(L, sp, c, smem, tmap, slot, mbar);
         else if constexpr (INGEST && G == 4 && std::is_same<TIn, uint8_t>::value && std::is_same<TS, uint16_t>::value)
             fused_cta_u8x2<TOut, G>(L, sp, c, smem);  // 16-bit sums: two groups per register
         else
-            fused_cta<TIn, TOut, uint32_t, TS, G, INGEST, true>(L, sp, c, smem);
+            fused_cta<TIn, TOut, uint32_t, TS, G, INGEST, true, false, false>(L, sp, c, smem);
     }
 }
 
 template <typename TIn, typename TOut, typename TS, bool INGEST>
-__device__ __forceinline__ void run_kind(const FusedLaunch& L, int G, int slot, unsigned item, unsigned upi,
-                                         unsigned units, unsigned char* smem) {
+__device__ __forceinline__ void run_kind(const FusedLaunch& L, int G, int slot, unsigned item, unsigned tpi,
+                                         unsigned cps, unsigned char* smem) {
     switch (G) {
-    case 2: run_g<TIn, TOut, TS, 2, INGEST>(L, slot, item, upi, units, smem); break;
-    case 3: run_g<TIn, TOut, TS, 3, INGEST>(L, slot, item, upi, units, smem); break;
-    default: run_g<TIn, TOut, TS, 4, INGEST>(L, slot, item, upi, units, smem); break;
+    case 2: run_g<TIn, TOut, TS, 2, INGEST>(L, slot, item, tpi, cps, smem); break;
+    case 3: run_g<TIn, TOut, TS, 3, INGEST>(L, slot, item, tpi, cps, smem); break;
+    default: run_g<TIn, TOut, TS, 4, INGEST>(L, slot, item, tpi, cps, smem); break;
     }
 }
 
@@ -175,33 +177,33 @@ __global__ void __launch_bounds__(256, 2) planes_batched(const __grid_constant__
         const FusedLaunch& L = B.pass[p];
         const int G = B.G[p];
         const int ik = B.in_kind[p], ok = B.out_kind[p];
-        const unsigned upi = B.upi[p], units = B.units[p];
+        const unsigned tpi = B.tpi[p], cps = B.cps[p];
         if (p == 0) {
-            if (ok == (int)ElemKind::U16) run_kind<uint8_t, uint16_t, uint16_t, true>(L, G, slot, cta, upi, units, smem);
-            else run_kind<uint8_t, uint32_t, uint16_t, true>(L, G, slot, cta, upi, units, smem);
+            if (ok == (int)ElemKind::U16) run_kind<uint8_t, uint16_t, uint16_t, true>(L, G, slot, cta, tpi, cps, smem);
+            else run_kind<uint8_t, uint32_t, uint16_t, true>(L, G, slot, cta, tpi, cps, smem);
         } else if (B.tma[p]) {
             // 16-bit input staged by TMA (G >= 3)
             const CUtensorMap* tm = &B.tmap[p];
             if (G == 4) {
                 if (ok == (int)ElemKind::U16)
-                    run_g<uint16_t, uint16_t, uint32_t, 4, false, true>(L, slot, cta, upi, units, smem, tm, mbar,
+                    run_g<uint16_t, uint16_t, uint32_t, 4, false, true>(L, slot, cta, tpi, cps, smem, tm, mbar,
                                                                         A.status);
                 else
-                    run_g<uint16_t, uint32_t, uint32_t, 4, false, true>(L, slot, cta, upi, units, smem, tm, mbar,
+                    run_g<uint16_t, uint32_t, uint32_t, 4, false, true>(L, slot, cta, tpi, cps, smem, tm, mbar,
                                                                         A.status);
             } else {
                 if (ok == (int)ElemKind::U16)
-                    run_g<uint16_t, uint16_t, uint32_t, 3, false, true>(L, slot, cta, upi, units, smem, tm, mbar,
+                    run_g<uint16_t, uint16_t, uint32_t, 3, false, true>(L, slot, cta, tpi, cps, smem, tm, mbar,
                                                                         A.status);
                 else
-                    run_g<uint16_t, uint32_t, uint32_t, 3, false, true>(L, slot, cta, upi, units, smem, tm, mbar,
+                    run_g<uint16_t, uint32_t, uint32_t, 3, false, true>(L, slot, cta, tpi, cps, smem, tm, mbar,
                                                                         A.status);
             }
         } else if (ik == (int)ElemKind::U16) {
-            if (ok == (int)ElemKind::U16) run_kind<uint16_t, uint16_t, uint32_t, false>(L, G, slot, cta, upi, units, smem);
-            else run_kind<uint16_t, uint32_t, uint32_t, false>(L, G, slot, cta, upi, units, smem);
+            if (ok == (int)ElemKind::U16) run_kind<uint16_t, uint16_t, uint32_t, false>(L, G, slot, cta, tpi, cps, smem);
+            else run_kind<uint16_t, uint32_t, uint32_t, false>(L, G, slot, cta, tpi, cps, smem);
         } else {
-            run_kind<uint32_t, uint32_t, uint32_t, false>(L, G, slot, cta, upi, units, smem);
+            run_kind<uint32_t, uint32_t, uint32_t, false>(L, G, slot, cta, tpi, cps, smem);
         }
         // Signal completion only where a later pass depends on it.
         if (p + 1 < B.npass) {
@@ -254,6 +256,9 @@ struct drt3d_batch_plan {
     int device = 0;
     int* d_status = nullptr;
     std::vector<FusedSchedule> sched;  // per volume
+    // Work-item size of the persistent launch per volume size: unit-tiles per
+    // item of each pass (0 or absent: the default of item_tiles_default).
+    std::map<int, std::vector<int>> item_tiles;
     // bound state
     bool bound = false;
     BatchVol* d_vols = nullptr;
@@ -323,6 +328,12 @@ void free_bound(drt3d_batch_plan* B) {
 
 size_t vol_ws_bytes(const FusedSchedule& S) { return S.npass > 1 ? (size_t)kMaxSlots * 2 * S.buf_bytes : 0; }
 
+// Default work-item size in unit-tiles: 8 tiles at G = 4 (measured best among
+// 1..48 on the N = 256 and N = 128 batches: shorter items pay their claim,
+// dependency check and completion signal too often, longer ones balance
+// worse), otherwise `upi` whole units.
+unsigned item_tiles_default(int G, unsigned upi, int ntiles) { return G >= 4 ? 8u : upi * (unsigned)ntiles; }
+
 }  // namespace
 
 extern "C" {
@@ -370,6 +381,19 @@ drt3d_status drt3d_batch_set_schedule(drt3d_batch_plan* B, int N, int ngroups, c
     if (!make_fused_schedule_groups(N, B->dtype, ngroups, G, &S)) return DRT3D_ERR_INVALID_ARG;
     for (int i = 0; i < B->count; ++i)
         if (B->Ns[i] == N) B->sched[i] = S;
+    B->item_tiles.erase(N);  // sized for the previous schedule's passes
+    if (B->bound) free_bound(B);
+    return DRT3D_OK;
+}
+
+drt3d_status drt3d_batch_set_item_tiles(drt3d_batch_plan* B, int N, int npass, const int* tiles) {
+    if (!B || !tiles) return DRT3D_ERR_INVALID_ARG;
+    const int i = (int)(std::find(B->Ns.begin(), B->Ns.end(), N) - B->Ns.begin());
+    if (i == B->count) return DRT3D_ERR_SIZE;  // no volume of this size in the batch
+    if (npass != B->sched[i].npass) return DRT3D_ERR_INVALID_ARG;
+    for (int p = 0; p < npass; ++p)
+        if (tiles[p] < 0) return DRT3D_ERR_INVALID_ARG;
+    B->item_tiles[N].assign(tiles, tiles + npass);
     if (B->bound) free_bound(B);
     return DRT3D_OK;
 }
@@ -440,9 +464,12 @@ drt3d_status drt3d_batch_bind(drt3d_batch_plan* B, const drt3d_vol_desc* descs, 
             // Small units (2^G x 2^G rows) are grouped so that an item carries
             // at least 256 rows: its claim, dependency wait and barriers would
             // otherwise cost more than its work.
-            bv.units[p] = (unsigned)(L.ctas / L.ntiles);
-            bv.upi[p] = ps.G >= 4 ? 1u : (ps.G == 3 ? 4u : (ps.G == 2 ? 16u : 64u));
-            bv.ctas[p] = (bv.units[p] + bv.upi[p] - 1) / bv.upi[p];
+            bv.cps[p] = (unsigned)L.ctas;
+            const unsigned upi = ps.G >= 4 ? 1u : (ps.G == 3 ? 4u : (ps.G == 2 ? 16u : 64u));
+            const auto it = B->item_tiles.find(N);
+            const int want = it != B->item_tiles.end() && p < (int)it->second.size() ? it->second[p] : 0;
+            bv.tpi[p] = want > 0 ? std::min((unsigned)want, bv.cps[p]) : item_tiles_default(ps.G, upi, L.ntiles);
+            bv.ctas[p] = (bv.cps[p] + bv.tpi[p] - 1) / bv.tpi[p];
         }
         B->vol_slot_stride.push_back(2 * buf);
         ws += align_up(vol_ws_bytes(S), 256);

@@ -55,6 +55,33 @@ def test_schedule_overrides_give_identical_results(drt):
             plan.set_schedule(old)
 
 
+@pytest.mark.parametrize("tiles", [1, 3, 8, 1000])
+def test_item_sizes_give_identical_results(drt, tiles):
+    """Work items of 1, 3 (not a divisor of a unit's tiles), 8 and more than
+    a dodecant's unit-tiles, on every pass of every size."""
+    Ns = [16, 32, 64, 128, 256, 64]
+    vols = _vols(Ns, 80)
+    ref = [drt.planes_forward(v) for v in vols]
+    scheds = {16: (4,), 32: (3, 2), 64: (3, 3), 128: (4, 3), 256: (4, 4)}
+    bp = drt.BatchPlan(Ns, schedules=scheds, item_tiles={N: [tiles] * len(g) for N, g in scheds.items()})
+    outs = bp.bind(vols)
+    bp.run()
+    assert bp.device_error() == 0
+    for o, r in zip(outs, ref):
+        assert torch.equal(o, r)
+
+
+def test_item_size_arguments_are_checked(drt):
+    bp = drt.BatchPlan([32, 64], schedules={64: (3, 3)})
+    for N, tiles, code in [(64, [8], 1),        # two passes at N = 64: INVALID_ARG
+                           (128, [8, 8], 2),    # no volume of that size: SIZE
+                           (64, [8, -1], 1)]:   # negative: INVALID_ARG
+        with pytest.raises(drt.DRT3DError) as e:
+            bp.set_item_tiles(N, tiles)
+        assert e.value.code == code
+    bp.set_item_tiles(64, [0, 2])  # 0 keeps the default
+
+
 def test_config_c4_batch_matches_one_by_one(drt, oracle_mod):
     """96 volumes, sizes 16:30, 32:30, 64:20, 128:10, 256:6 shuffled."""
     sizes = synth.c4_sizes()
