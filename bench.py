@@ -528,7 +528,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
         line["lines_c3"] = bench_lines(drt3d, synth, dev)
         torch.cuda.empty_cache()
-        line["lsq_c5"] = bench_lsq(drt3d, synth, dev)
+        line["lsq_c5"] = bench_lsq(drt3d, synth, dev, tune=not args.no_tune)
         torch.cuda.empty_cache()
         line["drt2d_images"] = bench_drt2d(drt3d, synth, dev)
         torch.cuda.empty_cache()
@@ -748,11 +748,16 @@ def bench_press(drt3d, synth, dev) -> dict:
             "workload": "128^3 float32 phantom (6 solid ellipsoids), all 12 dodecants, multigrid down to N=1"}
 
 
-def bench_lsq(drt3d, synth, dev) -> dict:
-    """Config 5: one gradient step of the least-squares fit, 8 x 128^3 float32."""
+def bench_lsq(drt3d, synth, dev, tune: bool = True) -> dict:
+    """Config 5: one gradient step of the least-squares fit, 8 x 128^3 float32
+    (with ``tune``, the adjoint's split autotuned first)."""
     import torch
 
     N, B = 128, 8
+    if tune:
+        from paper_2501_13664_gb300 import autotune
+
+        autotune.tune_adjoint([N], torch.float32)  # applied to the shared float32 plan
     x = torch.from_numpy(synth.c5_batch(N=N, batch=B)).to(dev)
     b = torch.zeros((B, 12, N, N, 3 * N), dtype=torch.float32, device=dev)
 
@@ -779,7 +784,9 @@ def bench_lsq(drt3d, synth, dev) -> dict:
     t = sorted(_event_ms(step_fused, 5))[2]
     passes = profile_launches(drt3d.get_plan(N, torch.float32), step_fused)
     lib_ms = sum(e["ms"] for e in passes.values())
+    fplan = drt3d.get_plan(N, torch.float32)
     return {"ms_per_step": t, "volumes": B, "N": N, "passes": passes, "library_ms": lib_ms,
+            "schedule_forward": list(fplan.schedule()), "schedule_adjoint": list(fplan.adjoint_schedule()),
             "autograd_mse_ms_per_step": t_mse,
             "note": "one gradient step of 0.5||Ax - b||^2 for 8 volumes through torch.autograd: ms_per_step with "
                     "the library's least-squares loss (residual subtracted in the forward's last pass, "

@@ -26,7 +26,7 @@
  *    its calls share one scratch array).  A plan's device status word is then
  *    shared: an error recorded by one call is reported by whichever
  *    drt3d_get_device_error() on that plan comes next.  Plan creation and
- *    destruction, drt3d_plan_set_schedule and the profiling calls are not
+ *    destruction, the schedule setters and the profiling calls are not
  *    thread-safe for the same plan.
  *  - N = 2^n with 2 <= N <= 1024 (Algorithms 1 and 3 take log2 N stages;
  *    non-cubic sizes are left as future work in the paper's conclusions).
@@ -297,11 +297,23 @@ drt3d_status drt2d_workspace_bytes(const drt3d_plan* plan, int B, uint32_t quadr
 /* Stage-fusion schedule of the planes forward: the n = log2 N stages of
  * eq.(map3D) run in `ngroups` passes of G[0], G[1], ... stages on both axes
  * (each 1..4, summing to n).  The default is ceil(n/4) near-equal groups;
- * an autotuner may set another split.  Changing it changes the forward's
- * workspace size (query drt3d_workspace_bytes again), never its results.
+ * an autotuner may set another split.  Changing it changes the workspace
+ * sizes (query drt3d_workspace_bytes again); integer results never change,
+ * float32 results only through the order of the additions.
  * Errors: INVALID_ARG (bad split). */
 drt3d_status drt3d_plan_set_schedule(drt3d_plan* plan, int ngroups, const int* G);
 drt3d_status drt3d_plan_get_schedule(const drt3d_plan* plan, int* ngroups, int G[8]);
+/* Stage-fusion schedule of the planes adjoint (eq.(invmap3Dsummation)): the
+ * adjoint runs the transposes of the passes of this split, last first.  Every
+ * split of the stages gives the same operator, so the adjoint's split may
+ * differ from the forward's (an autotuner picks each for speed; integer
+ * results are identical, float32 results differ only in the order of the
+ * additions).  ngroups = 0 (G may be null) makes the adjoint follow the
+ * forward's schedule again (the default).  The get call reports the split
+ * in effect.  Changes the adjoint's workspace size.  Not thread-safe for the
+ * same plan.  Errors: INVALID_ARG (bad split). */
+drt3d_status drt3d_plan_set_adjoint_schedule(drt3d_plan* plan, int ngroups, const int* G);
+drt3d_status drt3d_plan_get_adjoint_schedule(const drt3d_plan* plan, int* ngroups, int G[8]);
 
 /* ---------------------------------------------------------------------
  * Batched planes forward: many uint8 volumes of sizes N in {16,...,256} in

@@ -108,6 +108,21 @@ class Plan:
         _abi.check(self._lib.drt3d_plan_get_schedule(self.handle, ctypes.byref(ng), arr), "drt3d_plan_get_schedule")
         return tuple(arr[i] for i in range(ng.value))
 
+    def set_adjoint_schedule(self, groups) -> None:
+        """Stage-fusion split of the planes adjoint; None or () follows the
+        forward's schedule (see drt3d_plan_set_adjoint_schedule)."""
+        groups = tuple(groups or ())
+        arr = (ctypes.c_int * max(1, len(groups)))(*[int(g) for g in groups])
+        _abi.check(self._lib.drt3d_plan_set_adjoint_schedule(self.handle, len(groups), arr),
+                   "drt3d_plan_set_adjoint_schedule")
+
+    def adjoint_schedule(self) -> tuple:
+        ng = ctypes.c_int()
+        arr = (ctypes.c_int * 8)()
+        _abi.check(self._lib.drt3d_plan_get_adjoint_schedule(self.handle, ctypes.byref(ng), arr),
+                   "drt3d_plan_get_adjoint_schedule")
+        return tuple(arr[i] for i in range(ng.value))
+
     def __del__(self):
         try:
             if getattr(self, "handle", None):

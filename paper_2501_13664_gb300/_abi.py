@@ -52,6 +52,8 @@ SIGNATURES = {
     "drt3d_batch_plan_destroy": (I, [P]),
     "drt3d_batch_set_schedule": (I, [P, I, I, ctypes.POINTER(I)]),
     "drt3d_batch_set_item_tiles": (I, [P, I, I, ctypes.POINTER(I)]),
+    "drt3d_plan_set_adjoint_schedule": (I, [P, I, ctypes.POINTER(I)]),
+    "drt3d_plan_get_adjoint_schedule": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
     "drt3d_batch_workspace_bytes": (I, [P, ctypes.POINTER(SZ)]),
     "drt3d_batch_bind": (I, [P, P, P, SZ]),
     "drt3d_planes_forward_batched": (I, [P, P]),

@@ -1,11 +1,14 @@
-"""Autotuner for the planes forward's stage-fusion schedule.
+"""Autotuner for the planes forward's and adjoint's stage-fusion schedules.
 
 For each size N the candidates are the ordered splits of the n = log2 N
 stages into passes of 2..4 stages (each pass applies its stages on both
 axes).  Each candidate is timed with CUDA events on a seeded uint8 volume
 (all 12 dodecants, median of a few launches after warm-up) and the fastest
-is kept.  Results are cached as JSON keyed by device name, SM count, N and
-dtype, at $DRT3D_TUNE_CACHE or ~/.cache/drt3d/tune.json.
+is kept.  The adjoint's split is tuned on its own (``tune_adjoint``), and the
+persistent batched launch gets its own splits (``tune_batched``) and
+work-item lengths (``tune_batched_items``).  Results are cached as JSON
+keyed by device name, SM count, N and dtype, at $DRT3D_TUNE_CACHE or
+~/.cache/drt3d/tune.json.
 """
 from __future__ import annotations
 
@@ -15,7 +18,7 @@ import os
 
 import torch
 
-from . import ALL, get_plan, planes_forward
+from . import ALL, get_plan, planes_adjoint, planes_forward
 
 
 def splits(n: int, lo: int = 2, hi: int = 4) -> list:
@@ -82,6 +85,60 @@ def time_schedule(vol: torch.Tensor, groups, reps: int = 5) -> float:
         return times[len(times) // 2]
     finally:
         plan.set_schedule(old)
+
+
+def time_adjoint(N: int, groups, dtype: torch.dtype = torch.float32, reps: int = 7, seed: int = 13) -> float:
+    """Median milliseconds of the 12-dodecant planes adjoint under ``groups``
+    (the plan's adjoint schedule is restored afterwards)."""
+    plan = get_plan(N, dtype)
+    old = plan.adjoint_schedule() if plan.adjoint_schedule() != plan.schedule() else ()
+    plan.set_adjoint_schedule(groups)
+    try:
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        if dtype == torch.float32:
+            cot = torch.randn((12, N, N, 3 * N), generator=g).cuda()
+        else:
+            cot = torch.randint(-1000, 1000, (12, N, N, 3 * N), generator=g, dtype=torch.int32).cuda()
+        out = torch.empty((N, N, N), dtype=cot.dtype, device=cot.device)
+        ws = plan.workspace("planes_adjoint")
+        for _ in range(2):
+            planes_adjoint(cot, ALL, out=out, workspace=ws)
+        times = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            planes_adjoint(cot, ALL, out=out, workspace=ws)
+            b.record()
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        times.sort()
+        return times[len(times) // 2]
+    finally:
+        plan.set_adjoint_schedule(old)
+
+
+def tune_adjoint(Ns, dtype: torch.dtype = torch.float32, use_cache: bool = True, apply: bool = True) -> dict:
+    """{N: best split of the planes adjoint} (timed on its own: the adjoint's
+    transposed passes favour other splits than the forward's), applied to the
+    shared plans with ``apply``."""
+    cache = load_cache() if use_cache else {}
+    best = {}
+    for N in sorted(set(int(n) for n in Ns)):
+        key = "adjoint|" + _key(N, dtype)
+        if key in cache:
+            best[N] = tuple(cache[key]["groups"])
+        else:
+            n = N.bit_length() - 1
+            results = {str(s): time_adjoint(N, s, dtype) for s in splits(n)}
+            pick = min(results, key=results.get)
+            best[N] = tuple(int(x) for x in pick.strip("()").split(",") if x.strip())
+            cache[key] = {"groups": list(best[N]), "ms": results}
+            torch.cuda.empty_cache()
+        if apply:
+            get_plan(N, dtype).set_adjoint_schedule(best[N])
+    if use_cache:
+        save_cache(cache)
+    return best
 
 
 def tune(Ns, dtype: torch.dtype = torch.uint8, use_cache: bool = True, seed: int = 11) -> dict:

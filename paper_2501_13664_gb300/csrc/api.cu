@@ -217,8 +217,10 @@ static size_t djt_adj_slot_bytes(int N) {
 
 // One intermediate buffer of the planes adjoint: a fused pass's 32-bit rows,
 // or the dodecant's frame volume that the last pass writes.
+static const FusedSchedule& adjoint_schedule(const drt3d_plan* P) { return P->has_adj ? P->adj : P->fused; }
+
 static size_t adjoint_buf_bytes(const drt3d_plan* P) {
-    return std::max(P->fused.buf_bytes, align_up((size_t)P->N * P->N * P->N * 4, 256));
+    return std::max(adjoint_schedule(P).buf_bytes, align_up((size_t)P->N * P->N * P->N * 4, 256));
 }
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -585,7 +587,7 @@ drt3d_status drt3d_planes_adjoint(const drt3d_plan* P, const void* d_cot, void* 
     const int N = P->N;
     const bool is_float = P->dtype == DRT3D_F32;
     const size_t cot_block = (size_t)N * N * 3 * N * 4;
-    const FusedSchedule& S = P->fused;
+    const FusedSchedule& S = adjoint_schedule(P);
     char* ws = static_cast<char*>(d_ws);
 
     FusedLaunch L{};
@@ -1047,6 +1049,28 @@ drt3d_status drt3d_plan_get_schedule(const drt3d_plan* P, int* ngroups, int G[8]
     if (!P || !ngroups || !G) return DRT3D_ERR_INVALID_ARG;
     *ngroups = P->fused.npass;
     for (int g = 0; g < P->fused.npass; ++g) G[g] = P->fused.pass[g].G;
+    return DRT3D_OK;
+}
+
+drt3d_status drt3d_plan_set_adjoint_schedule(drt3d_plan* P, int ngroups, const int* G) {
+    if (!P) return DRT3D_ERR_INVALID_ARG;
+    if (ngroups == 0) {
+        P->has_adj = false;
+        return DRT3D_OK;
+    }
+    if (!G) return DRT3D_ERR_INVALID_ARG;
+    FusedSchedule S{};
+    if (!make_fused_schedule_groups(P->N, P->dtype, ngroups, G, &S)) return DRT3D_ERR_INVALID_ARG;
+    P->adj = S;
+    P->has_adj = true;
+    return DRT3D_OK;
+}
+
+drt3d_status drt3d_plan_get_adjoint_schedule(const drt3d_plan* P, int* ngroups, int G[8]) {
+    if (!P || !ngroups || !G) return DRT3D_ERR_INVALID_ARG;
+    const FusedSchedule& S = adjoint_schedule(P);
+    *ngroups = S.npass;
+    for (int g = 0; g < S.npass; ++g) G[g] = S.pass[g].G;
     return DRT3D_OK;
 }
 

@@ -325,6 +325,10 @@ struct drt3d_plan {
     int device;
     int* d_status;  // device status word (drt3d_status), 0 = OK
     drt3d::FusedSchedule fused;    // two-axis passes (forward)
+    // Passes of the adjoint when set (its own split of the stages: any split
+    // gives the same operator), else the forward's transposed.
+    drt3d::FusedSchedule adj;
+    bool has_adj = false;
     // Float32 plans of the coarser sizes N/2, N/4, ..., 2 used by the
     // iterative inverse, indexed by log2 of their size; host-only, created on
     // first use (by whichever host thread gets there first), sharing this

@@ -201,6 +201,33 @@ def test_adjoint_float_within_tolerance(drt, oracle_mod, N):
     assert np.all(np.abs(got - ref) <= FTOL * mag + 1e-30)
 
 
+@pytest.mark.parametrize("N,splits", [(64, [(3, 3), (2, 2, 2), (4, 2)]), (128, [(3, 2, 2), (2, 3, 2), (3, 4)])])
+def test_adjoint_schedule_of_its_own(drt, oracle_mod, N, splits):
+    """Any split of the stages gives the same adjoint: integer results equal
+    the oracle's under every adjoint split while the forward keeps its own,
+    float results stay within the bound; clearing it follows the forward."""
+    r = synth.random_int32((12, N, N, 3 * N), 16)
+    ref = oracle_mod.planes_adjoint(r)
+    rf = synth.random_float((12, N, N, 3 * N), 17)
+    reff = oracle_mod.planes_adjoint(rf.astype(np.float64))
+    mag = oracle_mod.planes_adjoint(np.abs(rf).astype(np.float64))
+    for dtype, cot in ((torch.int32, r), (torch.float32, rf)):
+        plan = drt.get_plan(N, dtype)
+        fwd = plan.schedule()
+        try:
+            for sp in splits:
+                plan.set_adjoint_schedule(sp)
+                assert plan.adjoint_schedule() == sp and plan.schedule() == fwd
+                got = drt.planes_adjoint(torch.from_numpy(cot).cuda()).cpu().numpy()
+                if dtype == torch.int32:
+                    np.testing.assert_array_equal(got, ref)
+                else:
+                    assert np.all(np.abs(got.astype(np.float64) - reff) <= FTOL * mag + 1e-30)
+        finally:
+            plan.set_adjoint_schedule(None)
+        assert plan.adjoint_schedule() == fwd
+
+
 def test_adjoint_is_deterministic(drt):
     N = 32
     r = torch.from_numpy(synth.random_float((12, N, N, 3 * N), 14)).cuda()
