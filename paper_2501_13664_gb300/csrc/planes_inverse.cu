@@ -432,10 +432,13 @@ planes_inv_pass(const __grid_constant__ InvLaunch L) {
 // nT[0] while base + i - S >= 0 and 0 below displacement 0.  Every later
 // access is then an aligned 16-byte vector at the lane's own chunk.  CH is
 // 4 VPL with VPL odd, so the 8 lanes of each quarter-warp phase of an LDS.128
-// or STS.128 at a stride of CH words touch 8 distinct bank groups.
+// or STS.128 at a stride of CH words touch 8 distinct bank groups (an even
+// VPL = 6 for rows of 768 was a third slower with its two-way conflicts).  A
+// pair is undone by a warp (LPP = 32 lanes) or, for rows of at most 320, by
+// a half-warp (LPP = 16: the narrowest span LPP CH >= W wins).
 //
-// The slots hold 32 CH words (the lanes' chunks) plus room for the shifted
-// block of the last lane.  Positions in [W, 32 CH) are zero at load; lo stays
+// The slots hold LPP CH words (the lanes' chunks) plus room for the shifted
+// block of the last lane.  Positions in [W, LPP CH) are zero at load; lo stays
 // zero there and hi is zero there whenever the pair passes the range check
 // (nT must vanish above W - 1 - S), so they never disturb the suffix sums of
 // data in the range of the forward map.
@@ -458,26 +461,52 @@ __device__ __forceinline__ void store_chunk(uint32_t* s, int c0, const uint32_t 
 // (j >= RR, this lane) or the previous lane's nT[c0 - RR + j] (j < RR); for
 // lane 0 those positions lie below S and take the fill value (nT[0] from
 // position fill_from on, 0 below).
-template <int CH, int RR>
+template <int CH, int RR, int LPP>
 __device__ __forceinline__ void realign(const uint32_t (&x)[CH], int lane, int sa, uint32_t nt0, int fill_from,
                                         uint32_t (&e)[CH]) {
 #pragma unroll
     for (int j = 0; j < RR; ++j) {
-        const uint32_t p = __shfl_up_sync(0xffffffffu, x[CH - RR + j], 1);
+        const uint32_t p = __shfl_up_sync(0xffffffffu, x[CH - RR + j], 1, LPP);
         e[j] = lane > 0 ? p : (sa + j >= fill_from ? nt0 : 0u);
     }
 #pragma unroll
     for (int j = RR; j < CH; ++j) e[j] = x[j - RR];
 }
 
-template <int CH>
+// The same with the previous lane's last three elements already shuffled in
+// (prev[k] = its x[CH - 3 + k]): no shuffle inside the branch on r.
+template <int CH, int RR>
+__device__ __forceinline__ void realign_from(const uint32_t (&x)[CH], const uint32_t (&prev)[3], int lane, int sa,
+                                             uint32_t nt0, int fill_from, uint32_t (&e)[CH]) {
+#pragma unroll
+    for (int j = 0; j < RR; ++j) e[j] = lane > 0 ? prev[3 - RR + j] : (sa + j >= fill_from ? nt0 : 0u);
+#pragma unroll
+    for (int j = RR; j < CH; ++j) e[j] = x[j - RR];
+}
+
+// r = S & 3 is uniform over a warp when a pair is the whole warp; with
+// half-warp pairs the two pairs of a warp have different slopes, so the
+// shuffles are done by every lane before branching on r.
+template <int CH, int LPP>
 __device__ __forceinline__ void realign_any(int r, const uint32_t (&x)[CH], int lane, int sa, uint32_t nt0,
                                             int fill_from, uint32_t (&e)[CH]) {
-    switch (r) {
-    case 0: realign<CH, 0>(x, lane, sa, nt0, fill_from, e); break;
-    case 1: realign<CH, 1>(x, lane, sa, nt0, fill_from, e); break;
-    case 2: realign<CH, 2>(x, lane, sa, nt0, fill_from, e); break;
-    default: realign<CH, 3>(x, lane, sa, nt0, fill_from, e); break;
+    if constexpr (LPP == 32) {
+        switch (r) {
+        case 0: realign<CH, 0, LPP>(x, lane, sa, nt0, fill_from, e); break;
+        case 1: realign<CH, 1, LPP>(x, lane, sa, nt0, fill_from, e); break;
+        case 2: realign<CH, 2, LPP>(x, lane, sa, nt0, fill_from, e); break;
+        default: realign<CH, 3, LPP>(x, lane, sa, nt0, fill_from, e); break;
+        }
+    } else {
+        uint32_t prev[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) prev[k] = __shfl_up_sync(0xffffffffu, x[CH - 3 + k], 1, LPP);
+        switch (r) {
+        case 0: realign_from<CH, 0>(x, prev, lane, sa, nt0, fill_from, e); break;
+        case 1: realign_from<CH, 1>(x, prev, lane, sa, nt0, fill_from, e); break;
+        case 2: realign_from<CH, 2>(x, prev, lane, sa, nt0, fill_from, e); break;
+        default: realign_from<CH, 3>(x, prev, lane, sa, nt0, fill_from, e); break;
+        }
     }
 }
 
@@ -500,23 +529,26 @@ __device__ __forceinline__ int phys_slot(int r) {
     return r;
 }
 
-// Per-CTA constants of the aligned-row kernel.
+// Per-CTA constants of the aligned-row kernel (lane: within the pair's LPP
+// lanes; pair: the pair of a stage this thread's lanes undo).
 struct InvCtx {
     uint32_t* rows;  // slot 0
-    int RS, W, base, sg, wq, j, m0, c0, lane, warp, LO, dlt;
+    int RS, W, base, sg, wq, j, m0, c0, lane, pair, LO, dlt;
     long long rs_axis, rs_other;
     bool direct;
 };
 
-// Undo stage J of the group (one pair per warp), in place in the slots; the
-// group's last stage (J = 0) with `direct` sends both rows out by bulk copies.
-template <int G, int VPL, int J>
+// Undo stage J of the group (one pair per LPP lanes), in place in the slots;
+// the group's last stage (J = 0) with `direct` sends both rows out by bulk
+// copies.
+template <int G, int VPL, int J, int LPP>
 __device__ __forceinline__ void inv_stage(const InvLaunch& L, const InvCtx& C, bool& bad) {
     constexpr int CH = 4 * VPL;
     constexpr int RUN = VPL;  // suffix-sum run length (4 runs per chunk)
+    constexpr int LOG_LPP = LPP == 32 ? 5 : 4;
     constexpr int half = 1 << J;
     const int lane = C.lane, c0 = C.c0, W = C.W;
-    const int p = C.warp;  // one pair per warp
+    const int p = C.pair;
     const int q = p >> J, tau = p & (half - 1);
     const int r0 = 2 * tau + (q << (J + 1));
     const int S = (C.sg << J) + tau;  // slope so far at global stage m0 + J
@@ -528,10 +560,10 @@ __device__ __forceinline__ void inv_stage(const InvLaunch& L, const InvCtx& C, b
     // data in the range has Delta = 0 above W - 1 - S (S < 2^(m0 + J))
     {
         bool top_bad = false;
-        if (C.m0 + J <= 5) {
+        if (C.m0 + J <= LOG_LPP) {
             if (lane < S) top_bad = s0[W - S + lane] != s1[W - S + lane];
         } else {
-            for (int i = W - S + lane; i < W; i += 32) top_bad |= s0[i] != s1[i];
+            for (int i = W - S + lane; i < W; i += LPP) top_bad |= s0[i] != s1[i];
         }
         if (__any_sync(0xffffffffu, top_bad) && lane == 0) flag(L.status, DRT3D_ERR_NOT_IN_RANGE);
     }
@@ -551,9 +583,9 @@ __device__ __forceinline__ void inv_stage(const InvLaunch& L, const InvCtx& C, b
     const uint32_t tot = x[0] + rc[0];
     uint32_t y = tot;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t z = __shfl_down_sync(0xffffffffu, y, off);
-        if (lane + off < 32) y += z;
+    for (int off = 1; off < LPP; off <<= 1) {
+        const uint32_t z = __shfl_down_sync(0xffffffffu, y, off, LPP);
+        if (lane + off < LPP) y += z;
     }
     const uint32_t carry = y - tot;  // chunks above this lane's
 #pragma unroll
@@ -564,17 +596,17 @@ __device__ __forceinline__ void inv_stage(const InvLaunch& L, const InvCtx& C, b
         a[k] -= x[k];         // lo = out_0 + T
     }
     store_chunk<CH>(s0, c0, a);
-    const uint32_t nt0 = __shfl_sync(0xffffffffu, x[0], 0);
+    const uint32_t nt0 = __shfl_sync(0xffffffffu, x[0], 0, LPP);
     const int r = S & 3, sa = S - r;
     const int fill_from = S - C.base;  // hi[i] = nT[0] for S - base <= i < S, 0 below
     {
         uint32_t e[CH];
-        realign_any<CH>(r, x, lane, sa, nt0, fill_from, e);  // hi over [c0 + sa, c0 + sa + CH)
+        realign_any<CH, LPP>(r, x, lane, sa, nt0, fill_from, e);  // hi over [c0 + sa, c0 + sa + CH)
         store_chunk<CH>(s1, c0 + sa, e);
     }
     // positions [0, sa) of hi lie below S
     if (4 * lane < sa) {
-        for (int v = lane; 4 * v < sa; v += 32) {
+        for (int v = lane; 4 * v < sa; v += LPP) {
             uint32_t f[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) f[k] = 4 * v + k >= fill_from ? nt0 : 0u;
@@ -589,7 +621,7 @@ __device__ __forceinline__ void inv_stage(const InvLaunch& L, const InvCtx& C, b
     // Values below LO must vanish; [dlt, W) of both rows leaves by two bulk
     // copies once this warp's writes are visible to the async proxy.
     __syncwarp();
-    for (int i = 4 * lane; i < C.LO; i += 128) {
+    for (int i = 4 * lane; i < C.LO; i += 4 * LPP) {
         const uint4 u0 = lds4(s0, i), u1 = lds4(s1, i);
         const uint32_t e0[4] = {u0.x | u1.x, u0.y | u1.y, u0.z | u1.z, u0.w | u1.w};
 #pragma unroll
@@ -621,25 +653,39 @@ __device__ __forceinline__ void inv_stage(const InvLaunch& L, const InvCtx& C, b
     }
 }
 
-template <int G, int VPL, int J>
+template <int G, int VPL, int J, int LPP>
 __device__ __forceinline__ void inv_stages(const InvLaunch& L, const InvCtx& C, bool& bad) {
-    inv_stage<G, VPL, J>(L, C, bad);
-    if constexpr (J > 0) inv_stages<G, VPL, J - 1>(L, C, bad);
+    inv_stage<G, VPL, J, LPP>(L, C, bad);
+    if constexpr (J > 0) inv_stages<G, VPL, J - 1, LPP>(L, C, bad);
 }
 
-template <int G, int VPL>
-__global__ void __launch_bounds__(inv_warps(G) * 32, (G >= 4 ? (VPL >= 7 ? 3 : 4) : (VPL >= 7 ? 5 : 8)))
+// Warps of the aligned-row kernel: 2^(G-1) pairs per stage, LPP lanes each.
+__host__ __device__ constexpr int inv_group_warps(int G, int LPP) { return (1 << (G - 1)) * LPP / 32; }
+
+// Minimum resident CTAs of the aligned-row kernel (register budget).
+__host__ __device__ constexpr int inv_group_min_ctas(int G, int VPL, int LPP) {
+    return LPP == 16 ? 8 : G >= 4 ? (VPL >= 7 ? 3 : 4) : (VPL >= 7 ? 5 : 8);
+}
+
+// LPP: lanes per pair, 32 (a warp) or 16 (a half-warp, for rows of at most
+// 64 VPL displacements: each lane then holds a wider chunk, fewer lanes idle
+// past the row, and the scans take four shuffle steps).
+template <int G, int VPL, int LPP>
+__global__ void __launch_bounds__(inv_group_warps(G, LPP) * 32, inv_group_min_ctas(G, VPL, LPP))
 planes_inv_group(const __grid_constant__ InvLaunch L) {
     pdl_wait_and_release();
+    static_assert(LPP == 32 || (LPP == 16 && G >= 2), "a pair is a warp or a half-warp");
     constexpr int R = 1 << G;
-    constexpr int NW = inv_warps(G);
+    constexpr int NW = inv_group_warps(G, LPP);
+    constexpr int NP = R / 2;  // pairs per stage
     constexpr int CH = 4 * VPL;
-    constexpr int SPAN = 32 * CH;
-    constexpr int RUN = VPL;  // suffix-sum run length (4 runs per chunk)
+    constexpr int SPAN = LPP * CH;
     extern __shared__ __align__(16) uint32_t rows_al[];
-    __shared__ __align__(8) uint64_t bar[NW];  // one per warp: its pair's two input rows
+    __shared__ __align__(8) uint64_t bar[NP];  // one per pair: its two input rows
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int pl = lane % LPP;                       // lane within the pair
+    const int pair = warp * (32 / LPP) + lane / LPP;  // the pair these lanes undo
     const int N = L.N, m0 = L.m0;
     const int base = L.gin.base;
     const int W = L.dmax - base;  // stored row length (a multiple of 4, at most SPAN)
@@ -651,7 +697,7 @@ planes_inv_group(const __grid_constant__ InvLaunch L) {
     const int j = (int)(unit >> wb);
     const long long rs_axis = L.axis == 0 ? N : 1;
     const long long rs_other = L.axis == 0 ? 1 : N;
-    const int c0 = lane * CH;
+    const int c0 = pl * CH;
     const Affine& M = L.map;
     // Final rows leave by bulk copies: buffer rows, or volume rows whose z'
     // runs forward in memory from a 16-byte-aligned start.
@@ -661,13 +707,13 @@ planes_inv_group(const __grid_constant__ InvLaunch L) {
     const int dlt = L.scatter ? 2 * N - base : L.gout.base - base;
     bool bad = false;
 
-    // ---- the warp's pair of the group's first stage: input rows o(2p),
-    // o(2p + 1) into slots 2p, 2p + 1 by two bulk copies; zeros past W.
+    // ---- the pair of the group's first stage: input rows o(2p), o(2p + 1)
+    // into slots 2p, 2p + 1 by two bulk copies; zeros past W.
     {
-        const int p = warp;
+        const int p = pair;
         uint32_t* s0 = rows_al + (2 * p) * RS;
         uint32_t* s1 = s0 + RS;
-        if (lane == 0) {
+        if (pl == 0) {
             tma::mbar_init(&bar[p], 1);
             tma::fence_barrier_init();
             const uint32_t* in = static_cast<const uint32_t*>(L.in);
@@ -677,13 +723,13 @@ planes_inv_group(const __grid_constant__ InvLaunch L) {
             tma::bulk_load(s0, g0, W * 4u, &bar[p]);
             tma::bulk_load(s1, g0 + rs_axis * L.gin.pitch, W * 4u, &bar[p]);
         }
-        for (int i = W + 4 * lane; i < SPAN; i += 128) {
+        for (int i = W + 4 * pl; i < SPAN; i += 4 * LPP) {
             sts4(s0, i, make_uint4(0u, 0u, 0u, 0u));
             sts4(s1, i, make_uint4(0u, 0u, 0u, 0u));
         }
         __syncwarp();
         if (!tma::mbar_wait(&bar[p], 0, kBulkWaitNs)) {
-            if (lane == 0) flag(L.status, DRT3D_ERR_TIMEOUT);
+            if (pl == 0) flag(L.status, DRT3D_ERR_TIMEOUT);
             tma::mbar_wait(&bar[p], 0, kBulkWaitNs);  // once more for the copies in flight
         }
     }
@@ -692,10 +738,10 @@ planes_inv_group(const __grid_constant__ InvLaunch L) {
         InvCtx C;
         C.rows = rows_al;
         C.RS = RS; C.W = W; C.base = base; C.sg = sg; C.wq = wq; C.j = j; C.m0 = m0;
-        C.c0 = c0; C.lane = lane; C.warp = warp; C.LO = LO; C.dlt = dlt;
+        C.c0 = c0; C.lane = pl; C.pair = pair; C.LO = LO; C.dlt = dlt;
         C.rs_axis = rs_axis; C.rs_other = rs_other;
         C.direct = direct;
-        inv_stages<G, VPL, G - 1>(L, C, bad);
+        inv_stages<G, VPL, G - 1, LPP>(L, C, bad);
     }
 
     if (!direct) {
@@ -738,24 +784,35 @@ planes_inv_group(const __grid_constant__ InvLaunch L) {
     if (__any_sync(0xffffffffu, bad) && lane == 0) flag(L.status, DRT3D_ERR_NOT_IN_RANGE);
 }
 
-// Chunk vectors per lane of the aligned-row kernel for rows of W displacements
-// (0 when the rows are too long or not made of whole 16-byte vectors).
-int inv_group_vpl(int W, const InvLaunch& L) {
+// Lanes per pair and chunk vectors per lane of the aligned-row kernel for rows
+// of W displacements: the narrowest span LPP * 4 VPL >= W (VPL odd, so the
+// lanes of a quarter-warp phase of a 16-byte access hit distinct bank groups;
+// half-warp pairs only for spans up to 320), a warp per pair on ties.
+// {0, 0} when the rows are too long or not made of whole 16-byte vectors.
+struct InvShape {
+    int lpp, vpl;
+};
+InvShape inv_group_shape(int W, int G, const InvLaunch& L) {
     if (W % 4 != 0 || L.gin.pitch % 4 != 0 || (!L.scatter && (L.gout.pitch % 4 != 0 || L.gout.base % 4 != 0)))
-        return 0;
-    for (int vpl : {1, 3, 5, 7})
-        if (W <= 128 * vpl) return vpl;
-    return 0;
+        return {0, 0};
+    InvShape best{0, 0};
+    for (InvShape c : {InvShape{32, 1}, InvShape{32, 3}, InvShape{32, 5}, InvShape{32, 7}, InvShape{16, 3},
+                       InvShape{16, 5}}) {
+        if (c.lpp == 16 && G < 2) continue;
+        const int span = c.lpp * 4 * c.vpl;
+        if (span >= W && (best.lpp == 0 || span < best.lpp * 4 * best.vpl)) best = c;
+    }
+    return best;
 }
 
-size_t inv_group_smem(int G, int m0, int vpl) {
-    return (size_t)(1 << G) * (32 * 4 * vpl + (((1 << (m0 + G - 1)) + 3) & ~3)) * 4;
+size_t inv_group_smem(int G, int m0, int vpl, int lpp) {
+    return (size_t)(1 << G) * (lpp * 4 * vpl + (((1 << (m0 + G - 1)) + 3) & ~3)) * 4;
 }
 
-template <int G, int VPL>
+template <int G, int VPL, int LPP>
 cudaError_t launch_inv_group(const InvLaunch& L, cudaStream_t s) {
-    const size_t smem = inv_group_smem(G, L.m0, VPL);
-    auto kern = planes_inv_group<G, VPL>;
+    const size_t smem = inv_group_smem(G, L.m0, VPL, LPP);
+    auto kern = planes_inv_group<G, VPL, LPP>;
     static DeviceOnce attr_done;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -763,21 +820,24 @@ cudaError_t launch_inv_group(const InvLaunch& L, cudaStream_t s) {
     if (!attr_done.done(dev)) {
         // the largest slot set this instantiation can need (m0 + G <= 10)
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)inv_group_smem(G, 10 - G, VPL));
+                                 (int)inv_group_smem(G, 10 - G, VPL, LPP));
         if (e != cudaSuccess) return e;
         attr_done.mark(dev);
     }
     const unsigned units = (unsigned)((long long)L.N << (L.n - G));
-    return launch_chained(kern, dim3(units), dim3(inv_warps(G) * 32), smem, s, L);
+    return launch_chained(kern, dim3(units), dim3(inv_group_warps(G, LPP) * 32), smem, s, L);
 }
 
 template <int G>
-cudaError_t launch_inv_group_g(const InvLaunch& L, int vpl, cudaStream_t s) {
-    switch (vpl) {
-    case 1: return launch_inv_group<G, 1>(L, s);
-    case 3: return launch_inv_group<G, 3>(L, s);
-    case 5: return launch_inv_group<G, 5>(L, s);
-    default: return launch_inv_group<G, 7>(L, s);
+cudaError_t launch_inv_group_g(const InvLaunch& L, InvShape sh, cudaStream_t s) {
+    if constexpr (G >= 2) {
+        if (sh.lpp == 16) return sh.vpl == 3 ? launch_inv_group<G, 3, 16>(L, s) : launch_inv_group<G, 5, 16>(L, s);
+    }
+    switch (sh.vpl) {
+    case 1: return launch_inv_group<G, 1, 32>(L, s);
+    case 3: return launch_inv_group<G, 3, 32>(L, s);
+    case 5: return launch_inv_group<G, 5, 32>(L, s);
+    default: return launch_inv_group<G, 7, 32>(L, s);
     }
 }
 
@@ -834,13 +894,13 @@ cudaError_t launch_inv_g(const InvLaunch& L, cudaStream_t s) {
 size_t inverse_smem_bytes(int N, int G, int base, int m0) { return inv_smem(G, 3 * N - base, m0); }
 
 cudaError_t launch_planes_inverse_pass(const InvLaunch& L, int G, cudaStream_t s) {
-    const int vpl = inv_group_vpl(L.dmax - L.gin.base, L);
-    if (vpl > 0) {
+    const InvShape sh = inv_group_shape(L.dmax - L.gin.base, G, L);
+    if (sh.vpl > 0) {
         switch (G) {
-        case 1: return launch_inv_group_g<1>(L, vpl, s);
-        case 2: return launch_inv_group_g<2>(L, vpl, s);
-        case 3: return launch_inv_group_g<3>(L, vpl, s);
-        case 4: return launch_inv_group_g<4>(L, vpl, s);
+        case 1: return launch_inv_group_g<1>(L, sh, s);
+        case 2: return launch_inv_group_g<2>(L, sh, s);
+        case 3: return launch_inv_group_g<3>(L, sh, s);
+        case 4: return launch_inv_group_g<4>(L, sh, s);
         }
         return cudaErrorInvalidValue;
     }
