@@ -531,6 +531,12 @@ static drt3d_status planes_forward_impl(const drt3d_plan* P, const void* d_in, v
         L.ctas = per_axis * per_axis * L.ntiles;
         L.vec_store = (ps.out.pitch % 4 == 0) && (ps.out.base % 4 == 0) && (3 * N) % 4 == 0;
         L.global_layout = (global && ps.final_) ? 1 : 0;
+        // Dispatch order of the slots alternates between passes, the last pass
+        // last to first: each pass starts on the slots whose input the previous
+        // pass wrote last (still in L2), and the first slot's output is the
+        // freshest in L2 when the call ends (a round trip inverts dodecant 0
+        // by default).
+        L.reverse_slots = ((S.npass - 1 - p) & 1) == 0 ? 1 : 0;
         char nm[40];
         std::snprintf(nm, sizeof nm, "planes_fused G=%d m0=%d", ps.G, ps.m0);
         prof_begin(P, stream, nm, nslots * fused_pass_bytes(P, ps));
@@ -611,6 +617,9 @@ drt3d_status drt3d_planes_adjoint(const drt3d_plan* P, const void* d_cot, void* 
         L.ntiles = (3 * N - PB - dfirst + V - 1) / V;
         const long long per_axis = 1LL << (P->n - ps.G);
         L.ctas = per_axis * per_axis * L.ntiles;
+        // slots first to last on the first adjoint pass (a forward's last pass
+        // ends on the first slot), then alternating (see planes_forward_impl)
+        L.reverse_slots = q & 1;
         FramesSum FS{};
         for (int k = 0, i = 0; k < 12; ++k) {
             if (!((mask >> k) & 1)) continue;

@@ -379,6 +379,7 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
                 (unsigned long long)blockIdx.y * gridDim.x + blockIdx.x + (unsigned)L.prefetch_ahead;
             const unsigned ny = (unsigned)(nxt / gridDim.x), nc = (unsigned)(nxt % gridDim.x);
             if (ny < gridDim.y) {
+                const int nsl = launch_slot(L.reverse_slots, ny, gridDim.y);
                 unsigned nu = nc / ntiles;
                 const int ntile = (int)(nc - nu * ntiles);
                 const int nsg1 = (int)(nu & ((1u << m0) - 1)); nu >>= m0;
@@ -392,7 +393,7 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
                     const int q = nd0 + nsg2 * u2 + nsg1 * u1;
                     // the loads read [q rounded down to 16 bytes, + WT + 16 bytes)
                     const int lo = max(q & ~(EA - 1), L.gin.base), hi = min(lo + WT + 2 * EA, L.dmax);
-                    const FusedSlot& ns = L.slot[ny];
+                    const FusedSlot& ns = L.slot[nsl];
                     const bool nswap = ns.swap != 0;
                     const int nrs1 = nswap ? 1 : N, nrs2 = nswap ? N : 1;
                     const long long row = (long long)(nsg1 + (u1 << m0) + (nwq1 << (m0 + G))) * nrs1 +

@@ -156,7 +156,15 @@ struct FusedLaunch {
     int* status;     // device status word (time-outs of staged loads), may be null
     int global_layout;  // last pass writes Algorithm 2's 4N x 4N x (3N - 2) array
     int prefetch_ahead;  // CTAs (in launch order) whose input rows a CTA prefetches into L2, 0 = none
+    // CTAs with blockIdx.y = j take slot nslots - 1 - j: the slots are
+    // dispatched last to first (an order only; buffers stay indexed by slot).
+    int reverse_slots;
 };
+
+// Slot of a CTA of a launch over `gridDim.y` slots (see reverse_slots).
+__device__ __forceinline__ int launch_slot(int reverse, unsigned y, unsigned ny) {
+    return reverse ? (int)(ny - 1 - y) : (int)y;
+}
 
 // One fused pass: G stages of eq.(map3D) (both axes).
 struct FusedPass {

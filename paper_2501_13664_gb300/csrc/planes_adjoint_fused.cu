@@ -90,7 +90,7 @@ planes_adj_fused(const __grid_constant__ FusedLaunch L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint32_t* S = reinterpret_cast<uint32_t*>(smem_raw);  // [u2][t1][WS], position p at p - SA
 
-    const FusedSlot& sp = L.slot[blockIdx.y];
+    const FusedSlot& sp = L.slot[launch_slot(L.reverse_slots, blockIdx.y, gridDim.y)];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool active = warp < NW;
     const int m0 = L.m0, N = L.N;
@@ -121,7 +121,7 @@ planes_adj_fused(const __grid_constant__ FusedLaunch L) {
             const int lo = max(a.d0, L.gin.base), hi = min(a.d0 + WT, L.dmax);
             if (a.d0 + PB < L.dmax && lo < hi) {
                 const int t1 = threadIdx.x / R, t2 = threadIdx.x % R;
-                const T* cot = static_cast<const T*>(L.slot[ny].in);
+                const T* cot = static_cast<const T*>(L.slot[launch_slot(L.reverse_slots, ny, gridDim.y)].in);
                 const T* rp = cot + ((a.o1base + t1) * N + a.o2base + t2) * L.gin.pitch - L.gin.base;
                 tma::prefetch_l2(rp + lo, (uint32_t)(hi - lo) * 4u);
             }

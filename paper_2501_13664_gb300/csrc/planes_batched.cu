@@ -105,6 +105,7 @@ __device__ __forceinline__ void run_g(const FusedLaunch& Lg, int slot, unsigned 
     L.ctas = Lg.ctas;
     L.vec_store = Lg.vec_store;
     L.prefetch_ahead = 0;  // launch order is not item order here (and the prefetch is compiled out)
+    L.reverse_slots = 0;
     L.status = status;
     L.global_layout = 0;
     const FusedSlot sp = Lg.slot[slot];

@@ -34,13 +34,14 @@ __global__ void __launch_bounds__(32 * fused_warps<G>(), (G >= 4 ? 2 : 1))
 planes_fused(const __grid_constant__ FusedLaunch L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_wait_and_release();
+    const int sl = launch_slot(L.reverse_slots, blockIdx.y, gridDim.y);
     if constexpr (INGEST && G == 4 && std::is_same<TIn, uint8_t>::value && std::is_same<TS, uint16_t>::value) {
-        if (!L.global_layout && !L.slot[blockIdx.y].sub)  // 16-bit sums: two groups per register
-            fused_cta_u8x2<TOut, G>(L, L.slot[blockIdx.y], blockIdx.x, smem_raw);
+        if (!L.global_layout && !L.slot[sl].sub)  // 16-bit sums: two groups per register
+            fused_cta_u8x2<TOut, G>(L, L.slot[sl], blockIdx.x, smem_raw);
         else
-            fused_cta<TIn, TOut, T, TS, G, INGEST, false>(L, L.slot[blockIdx.y], blockIdx.x, smem_raw);
+            fused_cta<TIn, TOut, T, TS, G, INGEST, false>(L, L.slot[sl], blockIdx.x, smem_raw);
     } else {
-        fused_cta<TIn, TOut, T, TS, G, INGEST, false>(L, L.slot[blockIdx.y], blockIdx.x, smem_raw);
+        fused_cta<TIn, TOut, T, TS, G, INGEST, false>(L, L.slot[sl], blockIdx.x, smem_raw);
     }
 }
 
@@ -83,8 +84,9 @@ planes_fused_tma(const __grid_constant__ FusedLaunch L, const __grid_constant__ 
     pdl_wait_and_release();
     // TMA destinations are kept 128-byte aligned.
     unsigned char* sm = smem_raw + ((128u - (tma::smem_u32(smem_raw) & 127u)) & 127u);
-    fused_cta<uint16_t, TOut, uint32_t, uint32_t, G, false, false, true>(L, L.slot[blockIdx.y], blockIdx.x, sm,
-                                                                        &tmap, (int)blockIdx.y, mbar);
+    const int sl = launch_slot(L.reverse_slots, blockIdx.y, gridDim.y);
+    fused_cta<uint16_t, TOut, uint32_t, uint32_t, G, false, false, true>(L, L.slot[sl], blockIdx.x, sm, &tmap, sl,
+                                                                        mbar);
 }
 
 template <typename TOut, int G>
