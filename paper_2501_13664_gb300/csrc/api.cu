@@ -542,7 +542,7 @@ static drt3d_status planes_forward_impl(const drt3d_plan* P, const void* d_in, v
         prof_begin(P, stream, nm, nslots * fused_pass_bytes(P, ps));
         cudaError_t e;
         if (fused_uses_tma(ps.G, ps.in_kind, ps.ingest))
-            e = launch_planes_fused_tma(L, ps.G, ps.out_kind, L.slot[0].in, 2 * buf, nslots, stream);
+            e = launch_planes_fused_tma(L, ps.G, ps.in_kind, ps.out_kind, L.slot[0].in, 2 * buf, nslots, stream);
         else
             e = launch_planes_fused(L, ps.G, ps.in_kind, ps.out_kind, ps.ingest, nslots, stream);
         if (e != cudaSuccess) return DRT3D_ERR_CUDA;

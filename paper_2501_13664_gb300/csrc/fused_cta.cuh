@@ -63,13 +63,29 @@ template <int G> __host__ __device__ constexpr int fused_ws() { return (fused_v<
 // on into the next row; for the last row, into this pad).
 template <int G> __host__ __device__ constexpr int fused_pad() { return WT - fused_ws<G>() > K ? WT - fused_ws<G>() : K; }
 
-// Staged (TMA) input of one phase-1 group: 2^G rows of WT + 8 16-bit
-// elements, the window [q, q + WT) of a row rounded out to 8-element (16-byte)
-// boundaries.  Each staged row starts 128 bytes after the previous one; the
-// staging of group u2 sits inside that group's block of phase-1 results,
-// which overwrites it once the group's warp has read it.
-constexpr int kStageElems = WT + 8;
-constexpr int kStageRowBytes = 384;
+// Staged (TMA) input of one phase-1 group: 2^G rows, each the window
+// [q, q + WT) of a row rounded out to 16-byte boundaries (WT + 16 / size
+// elements), rows ROW_BYTES apart (a multiple of 128 bytes, the alignment kept
+// for TMA destinations).  The staging of group u2 sits at the start of that
+// group's block of phase-1 results, which overwrites it once the group's warp
+// has read it; a group's block is the larger of the two (group_elems).
+template <typename TIn>
+struct Stage {
+    static constexpr int ELEMS = WT + 16 / (int)sizeof(TIn);
+    static constexpr int ROW_BYTES = (ELEMS * (int)sizeof(TIn) + 127) / 128 * 128;
+};
+constexpr int kStageElems = Stage<uint16_t>::ELEMS;
+constexpr int kStageRowBytes = Stage<uint16_t>::ROW_BYTES;
+
+// Elements (of the 32-bit phase-1 result type when staged) of one group's
+// block of shared memory: its 2^G result rows of WS, or its staging if that is
+// larger (32-bit rows).
+template <typename TIn, int G, bool TMA>
+__host__ __device__ constexpr int group_elems() {
+    return (!TMA || (1 << G) * fused_ws<G>() >= (1 << G) * Stage<TIn>::ROW_BYTES / 4)
+               ? (1 << G) * fused_ws<G>()
+               : (1 << G) * Stage<TIn>::ROW_BYTES / 4;
+}
 // Upper bound on a stalled transaction-count wait (ns): a load that has not
 // landed by then is reported as a time-out.
 constexpr unsigned long long kTmaWaitNs = 200000000ull;
@@ -177,6 +193,43 @@ __device__ __forceinline__ void unpack_u16(const Chunks16& w, T (&v)[K]) {
         const uint32_t word = x[e >> 1];
         v[i] = to_acc<uint16_t, T>((uint16_t)((e & 1) ? (word >> 16) : (word & 0xFFFFu)));
     }
+}
+
+template <typename T>
+__device__ __forceinline__ T from_bits(uint32_t x) {
+    if constexpr (std::is_same<T, float>::value) return __uint_as_float(x);
+    else return (T)x;
+}
+
+// Staged 32-bit rows of residue class J (u1 = J mod 4): the box starts at the
+// 4-aligned element below the window, so lane L's chunk is at 4L and its
+// elements are rr .. rr + 3 of the eight there (the second 16-byte read only
+// when rr > 0).
+template <int RR, typename T>
+__device__ __forceinline__ void take4_u32(const uint32_t* p, T (&v)[K]) {
+    const uint4 a = *reinterpret_cast<const uint4*>(p);
+    uint32_t x[8] = {a.x, a.y, a.z, a.w, 0u, 0u, 0u, 0u};
+    if constexpr (RR > 0) {
+        const uint4 b = *reinterpret_cast<const uint4*>(p + 4);
+        x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) v[i] = from_bits<T>(x[RR + i]);
+}
+
+template <int J, int G, typename T>
+__device__ __forceinline__ void stage_class_u32(int rr, const uint32_t* st, int lane, T (&v)[1 << G][K]) {
+    constexpr int RW = Stage<uint32_t>::ROW_BYTES / 4;  // words between staged rows
+#define DRT3D_STAGE_CLASS(RRV)                                  \
+    _Pragma("unroll") for (int u1 = J; u1 < (1 << G); u1 += 4) \
+        take4_u32<RRV, T>(st + u1 * RW + lane * K, v[u1]);
+    switch (rr) {
+    case 0: DRT3D_STAGE_CLASS(0) break;
+    case 1: DRT3D_STAGE_CLASS(1) break;
+    case 2: DRT3D_STAGE_CLASS(2) break;
+    default: DRT3D_STAGE_CLASS(3) break;
+    }
+#undef DRT3D_STAGE_CLASS
 }
 
 template <int J, int G, typename T>
@@ -308,14 +361,15 @@ template <typename TIn, typename TOut, typename T, typename TS, int G, bool INGE
 __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot& sp, unsigned cta,
                                           unsigned char* smem_raw, const CUtensorMap* tmap = nullptr,
                                           int slot_z = 0, uint64_t* mbar = nullptr) {
-    static_assert(!TMA || (sizeof(TIn) == 2 && !INGEST && sizeof(TS) == 4 && G >= 3),
-                  "TMA staging: 16-bit buffer input, 32-bit phase-1 results, G >= 3");
+    static_assert(!TMA || (!INGEST && sizeof(TS) == 4 && G >= 3 && (sizeof(TIn) == 2 || sizeof(TIn) == 4)),
+                  "TMA staging: 16- or 32-bit buffer input, 32-bit phase-1 results, G >= 3");
     // With TMA, `smem_raw` is 128-byte aligned and `mbar` holds 2^G barriers.
     constexpr int R = 1 << G;
     constexpr int NW = fused_warps<G>();
     constexpr int GPW = R / NW > 0 ? R / NW : 1;  // row groups per warp
     constexpr int WS = fused_ws<G>();
-    TS* S = reinterpret_cast<TS*>(smem_raw);  // [u2][t1][WS] (+ pad)
+    constexpr int GB = group_elems<TIn, G, TMA>();  // elements of one group's block
+    TS* S = reinterpret_cast<TS*>(smem_raw);  // [u2: GB][t1][WS] (+ pad)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool active = warp < NW;
     const int m0 = L.m0;
@@ -422,7 +476,7 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
                 const int u2 = warp + gi * NW;
                 const int g_lo = d0 + sg2 * u2, g_hi = g_lo + sg1 * (R - 1) + WT + 4;
                 if (g_hi <= L.gin.base || g_lo >= L.dmax) continue;
-                if (lane == 0) tma::mbar_arrive_expect_tx(&mbar[u2], R * kStageElems * 2);
+                if (lane == 0) tma::mbar_arrive_expect_tx(&mbar[u2], R * Stage<TIn>::ELEMS * (int)sizeof(TIn));
                 __syncwarp();
                 if (lane < R) {
                     if constexpr (COHERENT) tma::fence_proxy_async_global();  // rows other CTAs wrote
@@ -431,8 +485,9 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
                     const long long row =
                         (long long)(sg1 + (wq1 << (m0 + G))) * rs1 + (long long)a2 * rs2 + (long long)(u1 * rs1 << m0);
                     const int q = g_lo + sg1 * u1;
-                    unsigned char* dst = smem_raw + (size_t)u2 * R * WS * sizeof(TS) + u1 * kStageRowBytes;
-                    tma::load_3d(dst, tmap, (q & ~7) - L.gin.base, (int)row, slot_z, &mbar[u2]);
+                    unsigned char* dst = smem_raw + (size_t)u2 * GB * sizeof(TS) + u1 * Stage<TIn>::ROW_BYTES;
+                    constexpr int EA = 16 / (int)sizeof(TIn);  // elements per 16 bytes
+                    tma::load_3d(dst, tmap, (q & ~(EA - 1)) - L.gin.base, (int)row, slot_z, &mbar[u2]);
                 }
             }
         }
@@ -501,7 +556,7 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
                 if (lane * K < WS) {
 #pragma unroll
                     for (int t1 = 0; t1 < R; ++t1) {
-                        TS* dst = S + ((u2 * R + t1) * WS + lane * K);
+                        TS* dst = S + (u2 * GB + t1 * WS + lane * K);
 #pragma unroll
                         for (int i = 0; i < K; ++i) dst[i] = TS(0);
                     }
@@ -517,24 +572,37 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
                 if (!tma::mbar_wait(&mbar[u2], 0, kTmaWaitNs)) {
                     if (lane == 0 && L.status) atomicCAS(L.status, 0, (int)DRT3D_ERR_TIMEOUT);
                 }
-                // Two 8-byte reads per row from the 4-aligned element below the
-                // window; the in-chunk offset repeats with u1 mod 4 (as for the
-                // register path) and is unpacked at a compile-time offset.
-                const uint16_t* st = reinterpret_cast<const uint16_t*>(smem_raw + (size_t)u2 * R * WS * sizeof(TS));
-                const int g_lo = d0 + sg2 * u2;
-                Chunks16 w[R];
-#pragma unroll
-                for (int u1 = 0; u1 < R; ++u1) {
-                    const uint16_t* src = st + u1 * (kStageRowBytes / 2) + ((g_lo + sg1 * u1) & 4) + lane * K;
-                    w[u1].c[0] = *reinterpret_cast<const uint2*>(src);
-                    w[u1].c[1] = *reinterpret_cast<const uint2*>(src + 4);
-                }
-                __syncwarp();  // the group's results overwrite its staging
                 const int a = sg1 & 3, c = g_lo & 3;
-                unpack_class_u16<0, G>(c, w, v);
-                if constexpr (R > 1) unpack_class_u16<1, G>((c + a) & 3, w, v);
-                if constexpr (R > 2) unpack_class_u16<2, G>((c + 2 * a) & 3, w, v);
-                if constexpr (R > 3) unpack_class_u16<3, G>((c + 3 * a) & 3, w, v);
+                if constexpr (sizeof(TIn) == 2) {
+                    // Two 8-byte reads per row from the 4-aligned element below
+                    // the window; the in-chunk offset repeats with u1 mod 4 (as
+                    // for the register path) and is unpacked at a compile-time
+                    // offset.
+                    const uint16_t* st = reinterpret_cast<const uint16_t*>(smem_raw + (size_t)u2 * GB * sizeof(TS));
+                    Chunks16 w[R];
+#pragma unroll
+                    for (int u1 = 0; u1 < R; ++u1) {
+                        const uint16_t* src =
+                            st + u1 * (Stage<TIn>::ROW_BYTES / 2) + ((g_lo + sg1 * u1) & 4) + lane * K;
+                        w[u1].c[0] = *reinterpret_cast<const uint2*>(src);
+                        w[u1].c[1] = *reinterpret_cast<const uint2*>(src + 4);
+                    }
+                    __syncwarp();  // the group's results overwrite its staging
+                    unpack_class_u16<0, G>(c, w, v);
+                    if constexpr (R > 1) unpack_class_u16<1, G>((c + a) & 3, w, v);
+                    if constexpr (R > 2) unpack_class_u16<2, G>((c + 2 * a) & 3, w, v);
+                    if constexpr (R > 3) unpack_class_u16<3, G>((c + 3 * a) & 3, w, v);
+                } else {
+                    // 32-bit rows: one or two 16-byte reads per row at the
+                    // lane's chunk, taken by residue class at a compile-time
+                    // offset.
+                    const uint32_t* st = reinterpret_cast<const uint32_t*>(smem_raw + (size_t)u2 * GB * sizeof(TS));
+                    stage_class_u32<0, G>(c, st, lane, v);
+                    if constexpr (R > 1) stage_class_u32<1, G>((c + a) & 3, st, lane, v);
+                    if constexpr (R > 2) stage_class_u32<2, G>((c + 2 * a) & 3, st, lane, v);
+                    if constexpr (R > 3) stage_class_u32<3, G>((c + 3 * a) & 3, st, lane, v);
+                    __syncwarp();  // the group's results overwrite its staging
+                }
             } else if constexpr (sizeof(TIn) == 2) {
                 const int L0 = start - L.gin.base;  // window offset of row u1 = 0
                 const int width = L.dmax - L.gin.base;
@@ -579,7 +647,7 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
         if (lane * K < WS) {
 #pragma unroll
             for (int t1 = 0; t1 < R; ++t1) {
-                TS* dst = S + ((u2 * R + t1) * WS + lane * K);
+                TS* dst = S + (u2 * GB + t1 * WS + lane * K);
                 TS e[K];
 #pragma unroll
                 for (int i = 0; i < K; ++i) e[i] = (TS)v[t1][i];
@@ -614,7 +682,7 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
 #pragma unroll
         for (int u2 = 0; u2 < R; ++u2) {
             // lanes past WS read the next row (or the pad): values they feed are invalid
-            const TS* src = S + ((u2 * R + t1) * WS + lane * K);
+            const TS* src = S + (u2 * GB + t1 * WS + lane * K);
             TS e[K];
             if constexpr (sizeof(TS) == 4) {
                 uint4 w = *reinterpret_cast<const uint4*>(src);

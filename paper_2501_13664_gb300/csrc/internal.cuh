@@ -294,15 +294,16 @@ int fused_valid(int G);  // valid displacements per CTA tile of a G-stage fused 
 cudaError_t launch_planes_fused(const FusedLaunch& L, int G, ElemKind in_kind, ElemKind out_kind,
                                 bool ingest, int nslots, cudaStream_t s);
 // Whether a fused pass stages its input through TMA boxes (16-bit buffer
-// input, G >= 3), and that launch: `in_base` is slot 0's input buffer, the
-// other slots follow at `slot_stride` bytes.
+// input at G >= 3, 32-bit at G = 3), and that launch: `in_base` is slot 0's
+// input buffer, the other slots follow at `slot_stride` bytes.
 bool fused_uses_tma(int G, ElemKind in_kind, bool ingest);
-cudaError_t launch_planes_fused_tma(const FusedLaunch& L, int G, ElemKind out_kind, const void* in_base,
-                                    size_t slot_stride, int nslots, cudaStream_t s);
+cudaError_t launch_planes_fused_tma(const FusedLaunch& L, int G, ElemKind in_kind, ElemKind out_kind,
+                                    const void* in_base, size_t slot_stride, int nslots, cudaStream_t s);
 // The tensor map of those staged loads (x = displacement - base, y = row,
-// z = slot), for launches that keep it in global memory.
+// z = slot; elements of elem_bytes = 2 or 4), for launches that keep it in
+// global memory.
 cudaError_t encode_fused_tmap(const FusedLaunch& L, const void* in_base, size_t slot_stride, int nslots,
-                              CUtensorMap* map);
+                              int elem_bytes, CUtensorMap* map);
 // The transpose of one fused pass (planes_adjoint_fused.cu): reads the
 // forward pass's output rows (geometry gin) as cotangent and writes its input
 // rows (geometry gout; the frame volume, base 2N and pitch N, for the first

@@ -457,8 +457,9 @@ drt3d_status drt3d_batch_bind(drt3d_batch_plan* B, const drt3d_vol_desc* descs, 
                                    : ((p & 1) ? (void*)bufB : (void*)bufA);
             }
             bv.G[p] = ps.G;
-            bv.tma[p] = fused_uses_tma(ps.G, ps.in_kind, ps.ingest) ? 1 : 0;
-            if (bv.tma[p] && encode_fused_tmap(L, L.slot[0].in, 2 * buf, 12, &bv.tmap[p]) != cudaSuccess)
+            // (the persistent kernel stages 16-bit rows only)
+            bv.tma[p] = fused_uses_tma(ps.G, ps.in_kind, ps.ingest) && ps.in_kind == ElemKind::U16 ? 1 : 0;
+            if (bv.tma[p] && encode_fused_tmap(L, L.slot[0].in, 2 * buf, 12, 2, &bv.tmap[p]) != cudaSuccess)
                 return DRT3D_ERR_CUDA;
             bv.in_kind[p] = (int)ps.in_kind;
             bv.out_kind[p] = (int)ps.out_kind;
@@ -556,7 +557,8 @@ drt3d_status drt3d_planes_forward_batched(const drt3d_batch_plan* B, cudaStream_
                 const cudaStream_t st = B->streams[B->vol_stream[v]];
                 cudaError_t e;
                 if (bv.tma[p])
-                    e = launch_planes_fused_tma(L, bv.G[p], (ElemKind)bv.out_kind[p], L.slot[0].in,
+                    e = launch_planes_fused_tma(L, bv.G[p], (ElemKind)bv.in_kind[p], (ElemKind)bv.out_kind[p],
+                                                L.slot[0].in,
                                                 B->vol_slot_stride[v], 12, st);
                 else
                     e = launch_planes_fused(L, bv.G[p], (ElemKind)bv.in_kind[p], (ElemKind)bv.out_kind[p], p == 0,

@@ -73,10 +73,11 @@ cudaError_t launch_g(const FusedLaunch& Lin, int nslots, cudaStream_t s) {
     return launch_chained(kern, grid, dim3(32 * fused_warps<G>()), smem, s, L);
 }
 
-// Pass over 16-bit buffer rows with the phase-1 input staged by TMA: one
-// 1-row box per (u2, u1) row window, landing in the group's block of
-// phase-1 results; one mbarrier per group counts the bytes.
-template <typename TOut, int G>
+// Pass over buffer rows (16-bit, or 32-bit at G = 3) with the phase-1 input
+// staged by TMA: one 1-row box per (u2, u1) row window, landing in the
+// group's block of phase-1 results; one mbarrier per group counts the bytes.
+// T is the arithmetic type (uint32 ring or float), TIn the stored one.
+template <typename TIn, typename T, typename TOut, int G>
 __global__ void __launch_bounds__(32 * fused_warps<G>(), (G >= 4 ? 2 : 1))
 planes_fused_tma(const __grid_constant__ FusedLaunch L, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -85,14 +86,13 @@ planes_fused_tma(const __grid_constant__ FusedLaunch L, const __grid_constant__ 
     // TMA destinations are kept 128-byte aligned.
     unsigned char* sm = smem_raw + ((128u - (tma::smem_u32(smem_raw) & 127u)) & 127u);
     const int sl = launch_slot(L.reverse_slots, blockIdx.y, gridDim.y);
-    fused_cta<uint16_t, TOut, uint32_t, uint32_t, G, false, false, true>(L, L.slot[sl], blockIdx.x, sm, &tmap, sl,
-                                                                        mbar);
+    fused_cta<TIn, TOut, T, T, G, false, false, true>(L, L.slot[sl], blockIdx.x, sm, &tmap, sl, mbar);
 }
 
-template <typename TOut, int G>
+template <typename TIn, typename T, typename TOut, int G>
 cudaError_t launch_tma_g(const FusedLaunch& L, const CUtensorMap& map, int nslots, cudaStream_t s) {
-    const size_t smem = ((size_t)(1 << (2 * G)) * fused_ws<G>() + fused_pad<G>()) * 4 + 128;
-    auto kern = planes_fused_tma<TOut, G>;
+    const size_t smem = ((size_t)(1 << G) * group_elems<TIn, G, true>() + fused_pad<G>()) * 4 + 128;
+    auto kern = planes_fused_tma<TIn, T, TOut, G>;
     static DeviceOnce attr_done;  // per instantiation
     int dev = 0;
     cudaGetDevice(&dev);
@@ -179,37 +179,51 @@ cudaError_t launch_planes_fused(const FusedLaunch& L, int G, ElemKind in_kind, E
     return cudaErrorInvalidValue;
 }
 
+// 16-bit rows at G >= 3; 32-bit rows at G = 3 (at G = 4 their staging would
+// outgrow two CTAs' shared memory).
 bool fused_uses_tma(int G, ElemKind in_kind, bool ingest) {
-    return !ingest && in_kind == ElemKind::U16 && G >= 3;
+    if (ingest) return false;
+    if (in_kind == ElemKind::U16) return G >= 3;
+    return (in_kind == ElemKind::I32 || in_kind == ElemKind::F32) && G == 3;
 }
 
 cudaError_t encode_fused_tmap(const FusedLaunch& L, const void* in_base, size_t slot_stride, int nslots,
-                              CUtensorMap* map) {
+                              int elem_bytes, CUtensorMap* map) {
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return cudaErrorNotSupported;
     // 3-D view of the slots' input rows: x = displacement - base (the stored
     // width), y = row, z = slot.  Elements outside it read as zero.
     const cuuint64_t dims[3] = {(cuuint64_t)(L.dmax - L.gin.base), (cuuint64_t)L.N * L.N, (cuuint64_t)nslots};
-    const cuuint64_t strides[2] = {(cuuint64_t)L.gin.pitch * 2, (cuuint64_t)slot_stride};
-    const cuuint32_t box[3] = {(cuuint32_t)kStageElems, 1, 1};
+    if (elem_bytes != 2 && elem_bytes != 4) return cudaErrorInvalidValue;
+    const cuuint64_t strides[2] = {(cuuint64_t)L.gin.pitch * elem_bytes, (cuuint64_t)slot_stride};
+    const cuuint32_t box[3] = {(cuuint32_t)(elem_bytes == 2 ? Stage<uint16_t>::ELEMS : Stage<uint32_t>::ELEMS), 1, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<void*>(in_base), dims, strides, box,
+    const CUresult r = enc(map, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 3,
+                           const_cast<void*>(in_base), dims, strides, box,
                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch_planes_fused_tma(const FusedLaunch& L, int G, ElemKind out_kind, const void* in_base,
-                                    size_t slot_stride, int nslots, cudaStream_t s) {
+cudaError_t launch_planes_fused_tma(const FusedLaunch& L, int G, ElemKind in_kind, ElemKind out_kind,
+                                    const void* in_base, size_t slot_stride, int nslots, cudaStream_t s) {
+    if (!fused_uses_tma(G, in_kind, false)) return cudaErrorInvalidValue;
     CUtensorMap map;
-    const cudaError_t e = encode_fused_tmap(L, in_base, slot_stride, nslots, &map);
+    const cudaError_t e = encode_fused_tmap(L, in_base, slot_stride, nslots, elem_bytes(in_kind), &map);
     if (e != cudaSuccess) return e;
-    const bool to16 = out_kind == ElemKind::U16;
-    switch (G) {
-    case 3: return to16 ? launch_tma_g<uint16_t, 3>(L, map, nslots, s) : launch_tma_g<uint32_t, 3>(L, map, nslots, s);
-    case 4: return to16 ? launch_tma_g<uint16_t, 4>(L, map, nslots, s) : launch_tma_g<uint32_t, 4>(L, map, nslots, s);
+    if (in_kind == ElemKind::U16) {
+        const bool to16 = out_kind == ElemKind::U16;
+        if (G == 3)
+            return to16 ? launch_tma_g<uint16_t, uint32_t, uint16_t, 3>(L, map, nslots, s)
+                        : launch_tma_g<uint16_t, uint32_t, uint32_t, 3>(L, map, nslots, s);
+        return to16 ? launch_tma_g<uint16_t, uint32_t, uint16_t, 4>(L, map, nslots, s)
+                    : launch_tma_g<uint16_t, uint32_t, uint32_t, 4>(L, map, nslots, s);
     }
-    return cudaErrorInvalidValue;
+    if (in_kind == ElemKind::F32)
+        return out_kind == ElemKind::F32 ? launch_tma_g<float, float, float, 3>(L, map, nslots, s)
+                                         : cudaErrorInvalidValue;
+    return out_kind == ElemKind::I32 ? launch_tma_g<uint32_t, uint32_t, uint32_t, 3>(L, map, nslots, s)
+                                     : cudaErrorInvalidValue;
 }
 
 }  // namespace drt3d

@@ -25,6 +25,8 @@ on the device at most.
                     inverse (step sizes from the power iteration first)
     adj-f32-n128    N=128 float32 cotangent of all 12 dodecants (302 MB),
                     planes adjoint (backprojection) to the volume
+    fwd-f32-n128    one config-5 volume (N=128 float32, N(0,1)), forward of all
+                    12 dodecants (302 MB of float32 out)
 """
 from __future__ import annotations
 
@@ -41,7 +43,7 @@ def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("case", choices=["fused-n256-d1", "fused-n256", "inverse-n256", "lines-n64-s0", "batched-c4-n64",
                                      "lines-adj-n64", "drt2d-n256", "press-n64", "adj-f32-n128",
-                                     "lines-n128-s0"])
+                                     "lines-n128-s0", "fwd-f32-n128"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--schedule", type=str, default="4,4", help="stage-fusion split of the N=256 planes cases")
     args = ap.parse_args(argv)
@@ -121,6 +123,18 @@ def main(argv=None) -> int:
         torch.cuda.synchronize()
         status = plan.device_error()
         print(f"{args.case}: reps={args.reps} status={status} sum={float(back.double().sum()):.6e}")
+    elif args.case == "fwd-f32-n128":
+        N = 128
+        x = torch.from_numpy(synth.c5_batch(N=N, batch=1)[0]).to(dev)
+        plan = get_plan(N, torch.float32)
+        ws = plan.workspace("planes_forward")
+        out = torch.empty((12, N, N, 3 * N), dtype=torch.float32, device=dev)
+        for _ in range(args.reps):
+            planes_forward(x, ALL, out=out, workspace=ws)
+        torch.cuda.synchronize()
+        status = plan.device_error()
+        print(f"{args.case}: reps={args.reps} schedule={plan.schedule()} status={status} "
+              f"sum={float(out.double().sum()):.6e}")
     elif args.case in ("lines-n64-s0", "lines-n128-s0"):
         N = 64 if args.case == "lines-n64-s0" else 128
         vol = torch.from_numpy(synth.c3_volume(N)).to(dev)
