@@ -608,13 +608,29 @@ drt3d_status drt3d_planes_adjoint(const drt3d_plan* P, const void* d_cot, void* 
         L.m0 = ps.m0;
         L.gin = ps.out;                                // the forward pass's output rows
         L.gout = p == 0 ? Geo{2 * N, N} : ps.in;       // its input rows, or the frame volume
-        int V = 0, PB = 0;
-        adjoint_fused_tile(ps.G, &V, &PB);
-        L.V = V;
+        // Lanes of 4 positions (vector loads and stores), or of 5 where that
+        // cuts the positions computed by a quarter or more (a row that one
+        // 5-wide tile covers but 4-wide tiles need two for, as the frame rows
+        // of N = 128).
         const int R1 = (1 << ps.G) - 1;
         const int off_max = 2 * ((1 << ps.m0) - 1) * R1;
-        const int dfirst = (L.gout.base - PB - off_max) & ~3;
-        L.ntiles = (3 * N - PB - dfirst + V - 1) / V;
+        int KK = 4, V = 0, PB = 0;
+        adjoint_fused_tile(ps.G, 4, &V, &PB);
+        int ntiles = (3 * N - PB - ((L.gout.base - PB - off_max) & ~3) + V - 1) / V;
+        {
+            int V5 = 0, PB5 = 0;
+            if (adjoint_fused_tile(ps.G, 5, &V5, &PB5)) {
+                const int nt5 = (3 * N - PB5 - ((L.gout.base - PB5 - off_max) & ~3) + V5 - 1) / V5;
+                if (4 * (nt5 * 160) <= 3 * (ntiles * 128)) {
+                    KK = 5;
+                    V = V5;
+                    PB = PB5;
+                    ntiles = nt5;
+                }
+            }
+        }
+        L.V = V;
+        L.ntiles = ntiles;
         const long long per_axis = 1LL << (P->n - ps.G);
         L.ctas = per_axis * per_axis * L.ntiles;
         // slots first to last on the first adjoint pass (a forward's last pass
@@ -641,7 +657,7 @@ drt3d_status drt3d_planes_adjoint(const drt3d_plan* P, const void* d_cot, void* 
         const double rd = ps.final_ ? (double)N * N * 3 * N * 4 : (double)N * N * (3 * N - lo_out) * 4;
         const double wr = p == 0 ? (double)N * N * N * 4 : (double)N * N * (3 * N - lo_in) * 4;
         prof_begin(P, stream, nm, nslots * (rd + wr));
-        if (launch_planes_adjoint_fused(L, ps.G, is_float, nslots, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
+        if (launch_planes_adjoint_fused(L, ps.G, KK, is_float, nslots, stream) != cudaSuccess) return DRT3D_ERR_CUDA;
         prof_end(P, stream);
         if (p == 0) {
             // the frames summed through the dodecant maps, in increasing k so

@@ -308,8 +308,9 @@ cudaError_t encode_fused_tmap(const FusedLaunch& L, const void* in_base, size_t 
 // forward pass's output rows (geometry gin) as cotangent and writes its input
 // rows (geometry gout; the frame volume, base 2N and pitch N, for the first
 // pass).  `V` stored positions per tile; tile origins are placed by the kernel.
-void adjoint_fused_tile(int G, int* V, int* PB);
-cudaError_t launch_planes_adjoint_fused(const FusedLaunch& L, int G, bool is_float, int nslots, cudaStream_t s);
+bool adjoint_fused_tile(int G, int KK, int* V, int* PB);
+cudaError_t launch_planes_adjoint_fused(const FusedLaunch& L, int G, int KK, bool is_float, int nslots,
+                                        cudaStream_t s);
 
 }  // namespace drt3d
 

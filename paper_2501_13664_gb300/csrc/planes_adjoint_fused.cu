@@ -36,11 +36,24 @@ namespace {
 using namespace fused;
 
 // First valid (stored) phase-B position, stored positions per tile, first
-// phase-A position that phase B reads, and the shared-memory row width.
-template <int G> __host__ __device__ constexpr int adj_pb() { return (2 * ((1 << G) - 1) + 3) & ~3; }
-template <int G> __host__ __device__ constexpr int adj_v() { return G >= 4 ? 92 : WT - adj_pb<G>(); }
-template <int G> __host__ __device__ constexpr int adj_sa() { return (adj_pb<G>() - ((1 << G) - 1)) & ~3; }
-template <int G> __host__ __device__ constexpr int adj_ws() { return adj_pb<G>() + adj_v<G>() - adj_sa<G>(); }
+// phase-A position that phase B reads, and the shared-memory row width, for
+// lanes of KK positions (a warp tile of 32 KK).  All are multiples of KK, so
+// a lane's positions lie wholly inside or outside each range; with KK = 5
+// (G <= 3: rows of up to 140 stored positions in one tile, where 4-wide
+// lanes store at most 120) the stored width is also a multiple of 4, so tile
+// origins stay 16-byte aligned.
+template <int G, int KK> __host__ __device__ constexpr int adj_pb() {
+    return KK == 4 ? (2 * ((1 << G) - 1) + 3) & ~3 : (2 * ((1 << G) - 1) + KK - 1) / KK * KK;
+}
+template <int G, int KK> __host__ __device__ constexpr int adj_v() {
+    return KK == 4 ? (G >= 4 ? 92 : 32 * KK - adj_pb<G, KK>()) : (32 * KK - adj_pb<G, KK>()) / 20 * 20;
+}
+template <int G, int KK> __host__ __device__ constexpr int adj_sa() {
+    return (adj_pb<G, KK>() - ((1 << G) - 1)) / KK * KK;
+}
+template <int G, int KK> __host__ __device__ constexpr int adj_ws() {
+    return adj_pb<G, KK>() + adj_v<G, KK>() - adj_sa<G, KK>();
+}
 
 template <typename T>
 __device__ __forceinline__ T from_u32(uint32_t x) {
@@ -59,9 +72,9 @@ struct AdjTile {
     int d0;
 };
 
-template <int G>
+template <int G, int KK>
 __device__ __forceinline__ AdjTile adj_tile(const FusedLaunch& L, unsigned x) {
-    constexpr int PB = adj_pb<G>();
+    constexpr int PB = adj_pb<G, KK>();
     const unsigned ntiles = (unsigned)L.ntiles;
     unsigned unit = x / ntiles;
     const int tile = (int)(x - unit * ntiles);
@@ -73,20 +86,24 @@ __device__ __forceinline__ AdjTile adj_tile(const FusedLaunch& L, unsigned x) {
     AdjTile a;
     a.o1base = (sg1 << G) + ((long long)wq1 << (m0 + G));
     a.o2base = (sg2 << G) + ((long long)wq2 << (m0 + G));
-    a.d0 = ((L.gout.base - PB - (sg1 + sg2) * ((1 << G) - 1)) & ~3) + tile * adj_v<G>();
+    a.d0 = ((L.gout.base - PB - (sg1 + sg2) * ((1 << G) - 1)) & ~3) + tile * adj_v<G, KK>();
     return a;
 }
 
-template <typename T, int G>
+template <typename T, int G, int KK>
 __global__ void __launch_bounds__(32 * fused_warps<G>(), (G >= 4 ? 2 : 1))
 planes_adj_fused(const __grid_constant__ FusedLaunch L) {
     pdl_wait_and_release();
+    constexpr int K = KK;        // positions per lane (shadows the forward passes' 4)
+    constexpr int WT = 32 * KK;  // positions per warp tile
+    constexpr bool VEC = KK == 4;
     constexpr int R = 1 << G;
     constexpr int NW = fused_warps<G>();
     constexpr int GPW = R / NW > 0 ? R / NW : 1;  // row groups per warp
     constexpr int P0 = R - 1;
-    constexpr int PB = adj_pb<G>(), V = adj_v<G>(), SA = adj_sa<G>(), WS = adj_ws<G>();
-    static_assert(PB + V <= WT && SA + WS <= WT && WS % 4 == 0, "tile layout");
+    constexpr int PB = adj_pb<G, KK>(), V = adj_v<G, KK>(), SA = adj_sa<G, KK>(), WS = adj_ws<G, KK>();
+    static_assert(PB + V <= WT && SA + WS <= WT && (!VEC || WS % 4 == 0) && V % 4 == 0, "tile layout");
+    static_assert(PB % K == 0 && SA % K == 0 && V % K == 0, "lanes wholly inside or outside each range");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint32_t* S = reinterpret_cast<uint32_t*>(smem_raw);  // [u2][t1][WS], position p at p - SA
 
@@ -106,18 +123,19 @@ planes_adj_fused(const __grid_constant__ FusedLaunch L) {
     const int d0 = ((e_lo - PB - (sg1 + sg2) * P0) & ~3) + tile * V;  // tile origin, cotangent frame
     if (d0 + PB >= L.dmax) return;  // every row's first stored displacement lies past 3N
     const int p0 = lane * K;        // this lane's first position in the tile
-    const bool vec_in = (L.gin.pitch & 3) == 0 && (L.gin.base & 3) == 0 && (L.dmax & 3) == 0;
-    const bool vec_out = (L.gout.pitch & 3) == 0 && (e_lo & 3) == 0 && (L.dmax & 3) == 0;
+    const bool vec_in = VEC && (L.gin.pitch & 3) == 0 && (L.gin.base & 3) == 0 && (L.dmax & 3) == 0;
+    const bool vec_out = VEC && (L.gout.pitch & 3) == 0 && (e_lo & 3) == 0 && (L.dmax & 3) == 0;
 
     // Warm L2 with the cotangent rows of the CTA `prefetch_ahead` places later
     // in launch order (about one wave of resident CTAs): its loads then hit L2
     // instead of waiting on DRAM.  One row window per thread; a hint only.
-    if (L.prefetch_ahead > 0 && vec_in && threadIdx.x < R * R) {
+    if (L.prefetch_ahead > 0 && (L.gin.pitch & 3) == 0 && (L.gin.base & 3) == 0 && (L.dmax & 3) == 0 &&
+        threadIdx.x < R * R) {
         const unsigned long long next =
             (unsigned long long)blockIdx.y * gridDim.x + blockIdx.x + (unsigned)L.prefetch_ahead;
         const unsigned ny = (unsigned)(next / gridDim.x), nx = (unsigned)(next % gridDim.x);
         if (ny < gridDim.y) {
-            const AdjTile a = adj_tile<G>(L, nx);
+            const AdjTile a = adj_tile<G, KK>(L, nx);
             const int lo = max(a.d0, L.gin.base), hi = min(a.d0 + WT, L.dmax);
             if (a.d0 + PB < L.dmax && lo < hi) {
                 const int t1 = threadIdx.x / R, t2 = threadIdx.x % R;
@@ -143,10 +161,9 @@ planes_adj_fused(const __grid_constant__ FusedLaunch L) {
             if (vec_in) {
                 const bool in = pos >= L.gin.base && pos < L.dmax;
                 const uint4 w = in ? __ldg(reinterpret_cast<const uint4*>(rp + pos)) : make_uint4(0u, 0u, 0u, 0u);
-                v[t2][0] = from_u32<T>(w.x);
-                v[t2][1] = from_u32<T>(w.y);
-                v[t2][2] = from_u32<T>(w.z);
-                v[t2][3] = from_u32<T>(w.w);
+                const uint32_t e[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int i = 0; i < K; ++i) v[t2][i] = from_u32<T>(e[i % 4]);
             } else {
 #pragma unroll
                 for (int i = 0; i < K; ++i) {
@@ -158,9 +175,16 @@ planes_adj_fused(const __grid_constant__ FusedLaunch L) {
         adj_all<G, K>(v);  // rows t2 -> u2
         if (p0 >= SA && p0 < SA + WS) {
 #pragma unroll
-            for (int u2 = 0; u2 < R; ++u2)
-                *reinterpret_cast<uint4*>(S + (u2 * R + t1) * WS + (p0 - SA)) =
-                    make_uint4(to_u32(v[u2][0]), to_u32(v[u2][1]), to_u32(v[u2][2]), to_u32(v[u2][3]));
+            for (int u2 = 0; u2 < R; ++u2) {
+                uint32_t* dst = S + (u2 * R + t1) * WS + (p0 - SA);
+                if constexpr (VEC) {
+                    *reinterpret_cast<uint4*>(dst) =
+                        make_uint4(to_u32(v[u2][0]), to_u32(v[u2][1 % K]), to_u32(v[u2][2 % K]), to_u32(v[u2][3 % K]));
+                } else {
+#pragma unroll
+                    for (int i = 0; i < K; ++i) dst[i] = to_u32(v[u2][i]);
+                }
+            }
         }
     }
     __syncthreads();
@@ -173,11 +197,16 @@ planes_adj_fused(const __grid_constant__ FusedLaunch L) {
         T v[R][K];
 #pragma unroll
         for (int t1 = 0; t1 < R; ++t1) {
-            const uint4 w = *reinterpret_cast<const uint4*>(S + (u2 * R + t1) * WS + q);
-            v[t1][0] = from_u32<T>(w.x);
-            v[t1][1] = from_u32<T>(w.y);
-            v[t1][2] = from_u32<T>(w.z);
-            v[t1][3] = from_u32<T>(w.w);
+            const uint32_t* src = S + (u2 * R + t1) * WS + q;
+            if constexpr (VEC) {
+                const uint4 w = *reinterpret_cast<const uint4*>(src);
+                const uint32_t e[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int i = 0; i < K; ++i) v[t1][i] = from_u32<T>(e[i % 4]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < K; ++i) v[t1][i] = from_u32<T>(src[i]);
+            }
         }
         adj_all<G, K>(v);  // rows t1 -> u1
         const long long a2 = sg2 + (u2 << m0) + (wq2 << (m0 + G));
@@ -192,7 +221,7 @@ planes_adj_fused(const __grid_constant__ FusedLaunch L) {
                 const long long a1 = u1 + (wq1 << G);
                 T* dst = out + (a1 * N + a2) * L.gout.pitch + (e - e_lo);
                 *reinterpret_cast<uint4*>(dst) =
-                    make_uint4(to_u32(v[u1][0]), to_u32(v[u1][1]), to_u32(v[u1][2]), to_u32(v[u1][3]));
+                    make_uint4(to_u32(v[u1][0]), to_u32(v[u1][1 % K]), to_u32(v[u1][2 % K]), to_u32(v[u1][3 % K]));
             }
         } else {
 #pragma unroll
@@ -208,10 +237,10 @@ planes_adj_fused(const __grid_constant__ FusedLaunch L) {
     }
 }
 
-template <typename T, int G>
+template <typename T, int G, int KK>
 cudaError_t launch_adj_g(const FusedLaunch& Lin, int nslots, cudaStream_t s) {
-    const size_t smem = (size_t)(1 << (2 * G)) * adj_ws<G>() * 4;
-    auto kern = planes_adj_fused<T, G>;
+    const size_t smem = (size_t)(1 << (2 * G)) * adj_ws<G, KK>() * 4;
+    auto kern = planes_adj_fused<T, G, KK>;
     static DeviceOnce attr_done;           // per instantiation
     static std::atomic<int> wave[64] = {};  // resident CTAs of the device, written before the flag
     int dev = 0;
@@ -236,32 +265,50 @@ cudaError_t launch_adj_g(const FusedLaunch& Lin, int nslots, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t launch_adj_t(const FusedLaunch& L, int G, int nslots, cudaStream_t s) {
+cudaError_t launch_adj_t(const FusedLaunch& L, int G, int KK, int nslots, cudaStream_t s) {
+    if (KK == 5) {
+        switch (G) {
+        case 2: return launch_adj_g<T, 2, 5>(L, nslots, s);
+        case 3: return launch_adj_g<T, 3, 5>(L, nslots, s);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (G) {
-    case 1: return launch_adj_g<T, 1>(L, nslots, s);
-    case 2: return launch_adj_g<T, 2>(L, nslots, s);
-    case 3: return launch_adj_g<T, 3>(L, nslots, s);
-    case 4: return launch_adj_g<T, 4>(L, nslots, s);
+    case 1: return launch_adj_g<T, 1, 4>(L, nslots, s);
+    case 2: return launch_adj_g<T, 2, 4>(L, nslots, s);
+    case 3: return launch_adj_g<T, 3, 4>(L, nslots, s);
+    case 4: return launch_adj_g<T, 4, 4>(L, nslots, s);
     }
     return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-// Tile parameters of the fused adjoint: stored positions per tile, and the
-// first stored position (the tile origin sits that far below the first
-// displacement it stores for the unshifted row).
-void adjoint_fused_tile(int G, int* V, int* PB) {
-    switch (G) {
-    case 1: *V = adj_v<1>(); *PB = adj_pb<1>(); break;
-    case 2: *V = adj_v<2>(); *PB = adj_pb<2>(); break;
-    case 3: *V = adj_v<3>(); *PB = adj_pb<3>(); break;
-    default: *V = adj_v<4>(); *PB = adj_pb<4>(); break;
+// Tile parameters of the fused adjoint with lanes of KK positions (4, or 5
+// at G = 2, 3): stored positions per tile, and the first stored position (the
+// tile origin sits that far below the first displacement it stores for the
+// unshifted row).  False for an unsupported (G, KK).
+bool adjoint_fused_tile(int G, int KK, int* V, int* PB) {
+    if (KK == 5) {
+        switch (G) {
+        case 2: *V = adj_v<2, 5>(); *PB = adj_pb<2, 5>(); return true;
+        case 3: *V = adj_v<3, 5>(); *PB = adj_pb<3, 5>(); return true;
+        }
+        return false;
     }
+    if (KK != 4) return false;
+    switch (G) {
+    case 1: *V = adj_v<1, 4>(); *PB = adj_pb<1, 4>(); return true;
+    case 2: *V = adj_v<2, 4>(); *PB = adj_pb<2, 4>(); return true;
+    case 3: *V = adj_v<3, 4>(); *PB = adj_pb<3, 4>(); return true;
+    case 4: *V = adj_v<4, 4>(); *PB = adj_pb<4, 4>(); return true;
+    }
+    return false;
 }
 
-cudaError_t launch_planes_adjoint_fused(const FusedLaunch& L, int G, bool is_float, int nslots, cudaStream_t s) {
-    return is_float ? launch_adj_t<float>(L, G, nslots, s) : launch_adj_t<uint32_t>(L, G, nslots, s);
+cudaError_t launch_planes_adjoint_fused(const FusedLaunch& L, int G, int KK, bool is_float, int nslots,
+                                        cudaStream_t s) {
+    return is_float ? launch_adj_t<float>(L, G, KK, nslots, s) : launch_adj_t<uint32_t>(L, G, KK, nslots, s);
 }
 
 }  // namespace drt3d
