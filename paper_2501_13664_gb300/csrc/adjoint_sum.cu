@@ -31,7 +31,6 @@ struct Cube {
     static constexpr int WORDS = C * SX;
 };
 
-// Element e of a cube, local coordinates (e / C^2, (e / C) % C, e % C).
 template <typename T, int C>
 __global__ void __launch_bounds__(kSumThreads)
 frames_sum_kernel(const __grid_constant__ FramesSum S) {
@@ -44,65 +43,65 @@ frames_sum_kernel(const __grid_constant__ FramesSum S) {
     const int cx = (b / (nc * nc)) * C, cy = ((b / nc) % nc) * C, cz = (b % nc) * C;  // volume cube origin
     const int t = (int)threadIdx.x;
 
+    // Element e = t + 256 r of a cube is (x, y, z) = (xt + r XS, yt, zt): a
+    // thread's elements differ only in x, and y, z, xt depend on t alone.
+    constexpr int XS = kSumThreads / (C * C);
+    static_assert(kSumThreads % (C * C) == 0, "a cube layer divides the block");
+    const int xt = t / (C * C), yt = (t / C) % C, zt = t % C;
+    const bool live = Q::V >= kSumThreads || t < Q::V;
+
     T next[Q::PER];
     auto load = [&](int i) {
-        const T* F = static_cast<const T*>(S.frame[i]);
-        // frame cube origin (ox, oy, oz)
+        // frame cube origin (ox, oy, oz); the thread's elements along x'
         const int vx = pick(S.vaxis[i][0], cx, cy, cz), vy = pick(S.vaxis[i][1], cx, cy, cz),
                   vz = pick(S.vaxis[i][2], cx, cy, cz);
         const int ox = S.flip[i][0] ? N - C - vx : vx, oy = S.flip[i][1] ? N - C - vy : vy,
                   oz = S.flip[i][2] ? N - C - vz : vz;
+        const T* F = static_cast<const T*>(S.frame[i]) + ((long long)(ox + xt) * N + (oy + yt)) * N + (oz + zt);
+        const long long layer = (long long)XS * N * N;
 #pragma unroll
-        for (int r = 0; r < Q::PER; ++r) {
-            const int e = t + kSumThreads * r;
-            if (Q::V % kSumThreads == 0 || e < Q::V) {
-                const int x = e / (C * C), y = (e / C) % C, z = e % C;
-                next[r] = F[((long long)(ox + x) * N + (oy + y)) * N + (oz + z)];
-            }
-        }
+        for (int r = 0; r < Q::PER; ++r)
+            if (live) next[r] = F[r * layer];
     };
 
     T acc[Q::PER];
     load(0);
 #pragma unroll 1
     for (int i = 0; i < S.nslots; ++i) {
+        if (live) {
 #pragma unroll
-        for (int r = 0; r < Q::PER; ++r) {
-            const int e = t + kSumThreads * r;
-            if (Q::V % kSumThreads == 0 || e < Q::V) {
-                const int x = e / (C * C), y = (e / C) % C, z = e % C;
-                cube[x * Q::SX + y * Q::SY + z] = next[r];
-            }
+            for (int r = 0; r < Q::PER; ++r) cube[(xt + r * XS) * Q::SX + yt * Q::SY + zt] = next[r];
         }
         __syncthreads();
         if (i + 1 < S.nslots) load(i + 1);
-        // frame-local coordinates of each of the thread's volume-local voxels
-        const int ax0 = S.vaxis[i][0], ax1 = S.vaxis[i][1], ax2 = S.vaxis[i][2];
-        const bool f0 = S.flip[i][0], f1 = S.flip[i][1], f2 = S.flip[i][2];
+        // Shared-memory offset of the thread's volume-local voxel (xt + r XS,
+        // yt, zt) in frame i's cube: frame axis a holds volume axis vaxis[a]
+        // (reversed when flipped), so the offset is base + r dstep, dstep the
+        // step of the frame axis that holds volume x.
+        int base = 0, dstep = 0;
 #pragma unroll
-        for (int r = 0; r < Q::PER; ++r) {
-            const int v = t + kSumThreads * r;
-            if (Q::V % kSumThreads == 0 || v < Q::V) {
-                const int x = v / (C * C), y = (v / C) % C, z = v % C;
-                const int p0 = pick(ax0, x, y, z), p1 = pick(ax1, x, y, z), p2 = pick(ax2, x, y, z);
-                const int l0 = f0 ? C - 1 - p0 : p0;
-                const int l1 = f1 ? C - 1 - p1 : p1;
-                const int l2 = f2 ? C - 1 - p2 : p2;
-                const T val = cube[l0 * Q::SX + l1 * Q::SY + l2];
+        for (int a = 0; a < 3; ++a) {
+            const int va = S.vaxis[i][a];
+            const int pa = pick(va, xt, yt, zt);
+            const int st = a == 0 ? Q::SX : a == 1 ? Q::SY : 1;
+            const bool f = S.flip[i][a] != 0;
+            base += (f ? C - 1 - pa : pa) * st;
+            if (va == 0) dstep = (f ? -st : st) * XS;
+        }
+        if (live) {
+#pragma unroll
+            for (int r = 0; r < Q::PER; ++r) {
+                const T val = cube[base + r * dstep];
                 acc[r] = i == 0 ? val : T(acc[r] + val);
             }
         }
         __syncthreads();
     }
 
-    T* vol = static_cast<T*>(S.vol);
+    T* vol = static_cast<T*>(S.vol) + ((long long)(cx + xt) * N + (cy + yt)) * N + (cz + zt);
+    if (live) {
 #pragma unroll
-    for (int r = 0; r < Q::PER; ++r) {
-        const int v = t + kSumThreads * r;
-        if (Q::V % kSumThreads == 0 || v < Q::V) {
-            const int x = v / (C * C), y = (v / C) % C, z = v % C;
-            vol[((long long)(cx + x) * N + (cy + y)) * N + (cz + z)] = acc[r];
-        }
+        for (int r = 0; r < Q::PER; ++r) vol[(long long)r * XS * N * N] = acc[r];
     }
 }
 
