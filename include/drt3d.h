@@ -97,7 +97,8 @@ typedef enum drt3d_op {
     DRT3D_OP_PLANES_INVERSE = 2,
     DRT3D_OP_LINES_FORWARD = 3,
     DRT3D_OP_LINES_ADJOINT = 4,
-    DRT3D_OP_PLANES_PRESS = 5
+    DRT3D_OP_PLANES_PRESS = 5,
+    DRT3D_OP_PLANES_RESIDUAL_LOSS = 6
 } drt3d_op;
 
 #define DRT3D_ALL_DODECANTS 0xFFFu
@@ -177,6 +178,22 @@ drt3d_status drt3d_planes_forward_global(const drt3d_plan* plan, const void* d_i
 drt3d_status drt3d_planes_forward_residual(const drt3d_plan* plan, const void* d_in, const void* d_target,
                                            void* d_out, uint32_t dodecant_mask, void* d_ws, size_t ws_bytes,
                                            cudaStream_t stream);
+
+/* drt3d_planes_forward_residual, and the least-squares loss of that residual:
+ *   d_loss[0] = 0.5 * sum over the stored cells of (A x - b)^2   (double).
+ * Each cell's square is added as the last pass stores it (per thread in
+ * float, per CTA in double into the workspace), then one small launch adds
+ * the partial sums in a fixed order, so the loss is the same on every run
+ * and no extra pass reads the residual.  Float32 plans only; d_loss is
+ * device memory (8-byte aligned).  The workspace must hold
+ * drt3d_workspace_bytes(plan, DRT3D_OP_PLANES_RESIDUAL_LOSS) bytes (the
+ * forward's, then the partial sums).  No paper counterpart: the loss of
+ * Section 5.2's fit written into the transform's epilogue.
+ * Errors: as drt3d_planes_forward_residual; DTYPE for non-float plans,
+ * INVALID_ARG when d_loss is NULL. */
+drt3d_status drt3d_planes_forward_residual_loss(const drt3d_plan* plan, const void* d_in, const void* d_target,
+                                                void* d_out, uint32_t dodecant_mask, double* d_loss, void* d_ws,
+                                                size_t ws_bytes, cudaStream_t stream);
 
 /* Adjoint (backprojection) of drt3d_planes_forward (Section 5.1, stage loop
  * reversed with eq.(invmap3Dsummation); reads below d = 0 are zero):

@@ -290,6 +290,34 @@ def planes_forward_residual(vol: torch.Tensor, target: torch.Tensor, dodecants=A
     return out.to("cpu") if host else out
 
 
+def planes_forward_residual_loss(vol: torch.Tensor, target: torch.Tensor, dodecants=ALL,
+                                 out: torch.Tensor | None = None, loss: torch.Tensor | None = None,
+                                 workspace: torch.Tensor | None = None):
+    """(r, loss): r = A vol - target as ``planes_forward_residual`` (float32
+    volumes) and loss = 0.5 ||r||^2, a float64 cuda scalar summed as the
+    transform stores r (see drt3d_planes_forward_residual_loss)."""
+    vol_d, host = _to_device(vol)
+    N = _vol_check(vol_d)
+    if vol_d.dtype != torch.float32:
+        raise TypeError("the residual loss takes float32 volumes")
+    m = _mask(dodecants)
+    plan = get_plan(N, vol_d.dtype)
+    shape = (_count(m), N, N, 3 * N)
+    if (tuple(target.shape) != shape or target.dtype != torch.float32 or not target.is_cuda
+            or not target.is_contiguous()):
+        raise ValueError(f"target must be a contiguous cuda float32 tensor of shape {shape}")
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=vol_d.device)
+    if loss is None:
+        loss = torch.empty((), dtype=torch.float64, device=vol_d.device)
+    ws = workspace if workspace is not None else plan.workspace("planes_residual_loss")
+    _abi.check(plan._lib.drt3d_planes_forward_residual_loss(plan.handle, vol_d.data_ptr(), target.data_ptr(),
+                                                            out.data_ptr(), m, loss.data_ptr(), ws.data_ptr(),
+                                                            ws.numel(), _stream()),
+               "drt3d_planes_forward_residual_loss")
+    return (out.to("cpu"), loss.to("cpu")) if host else (out, loss)
+
+
 def planes_forward_global(vol: torch.Tensor, out: torch.Tensor | None = None,
                           workspace: torch.Tensor | None = None) -> torch.Tensor:
     """All 12 dodecants in Algorithm 2's global 4N x 4N x (3N-2) layout."""

@@ -53,6 +53,7 @@ SIGNATURES = {
     "drt3d_batch_set_schedule": (I, [P, I, I, ctypes.POINTER(I)]),
     "drt3d_batch_set_item_tiles": (I, [P, I, I, ctypes.POINTER(I)]),
     "drt3d_plan_set_adjoint_schedule": (I, [P, I, ctypes.POINTER(I)]),
+    "drt3d_planes_forward_residual_loss": (I, [P, P, P, P, U32, P, P, SZ, P]),
     "drt3d_plan_get_adjoint_schedule": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
     "drt3d_batch_workspace_bytes": (I, [P, ctypes.POINTER(SZ)]),
     "drt3d_batch_bind": (I, [P, P, P, SZ]),
@@ -71,7 +72,7 @@ STATUS = {
 }
 DTYPES = {"u8": 0, "i16": 1, "i32": 2, "f32": 3}
 OPS = {"planes_forward": 0, "planes_adjoint": 1, "planes_inverse": 2, "lines_forward": 3, "lines_adjoint": 4,
-       "planes_press": 5}
+       "planes_press": 5, "planes_residual_loss": 6}
 
 
 class DRT3DError(RuntimeError):

@@ -219,6 +219,17 @@ static size_t djt_adj_slot_bytes(int N) {
 // or the dodecant's frame volume that the last pass writes.
 static const FusedSchedule& adjoint_schedule(const drt3d_plan* P) { return P->has_adj ? P->adj : P->fused; }
 
+// Partial sums of the squared residual that the final forward pass writes for
+// one dodecant slot (drt3d_planes_forward_residual_loss): one per CTA of that
+// pass.
+static long long residual_partials_per_slot(const drt3d_plan* P) {
+    const FusedPass& ps = P->fused.pass[P->fused.npass - 1];
+    const int V = fused_valid(ps.G);
+    const long long ntiles = (3LL * P->N - ps.out.base + V - 1) / V;
+    const long long per_axis = 1LL << (P->n - ps.G);
+    return per_axis * per_axis * ntiles;
+}
+
 static size_t adjoint_buf_bytes(const drt3d_plan* P) {
     return std::max(adjoint_schedule(P).buf_bytes, align_up((size_t)P->N * P->N * P->N * 4, 256));
 }
@@ -442,6 +453,10 @@ drt3d_status drt3d_workspace_bytes(const drt3d_plan* P, int op, size_t* bytes) {
     case DRT3D_OP_PLANES_INVERSE:
         *bytes = 2 * inverse_buf_bytes(P->N);
         return DRT3D_OK;
+    case DRT3D_OP_PLANES_RESIDUAL_LOSS:
+        *bytes = align_up((size_t)kMaxSlots * 2 * P->fused.buf_bytes, 256) +
+                 (size_t)kMaxSlots * residual_partials_per_slot(P) * sizeof(double);
+        return DRT3D_OK;
     case DRT3D_OP_LINES_FORWARD:
         *bytes = (size_t)kMaxSlots * djt_buf_bytes(P->N);
         if (*bytes) *bytes += 2 * djt_frame_copy_bytes(P->N, P->dtype);
@@ -484,9 +499,12 @@ static void global_row_map(int N, int k, FusedSlot& fs) {
     fs.g2 = (int)(a[0][1] * W + a[1][1]);
 }
 
+// d_sub: residual target of the final pass (or null); d_sq: with d_sub and a
+// float32 plan, its per-CTA partial sums of the squared residual,
+// residual_partials_per_slot per slot (or null).
 static drt3d_status planes_forward_impl(const drt3d_plan* P, const void* d_in, void* d_out, uint32_t mask,
                                         void* d_ws, size_t ws_bytes, cudaStream_t stream, bool global,
-                                        const void* d_sub = nullptr) {
+                                        const void* d_sub = nullptr, double* d_sq = nullptr) {
     if (!P || !d_in || !d_out) return DRT3D_ERR_INVALID_ARG;
     if (d_sub && (global || !aligned16(d_sub))) return d_sub && global ? DRT3D_ERR_INVALID_ARG : DRT3D_ERR_ALIGN;
     if (!device_is_current(P->device)) return DRT3D_ERR_INVALID_ARG;
@@ -519,6 +537,7 @@ static drt3d_status planes_forward_impl(const drt3d_plan* P, const void* d_in, v
                                : ((p & 1) ? (void*)bufB : (void*)bufA);
             fs.sub = (ps.final_ && d_sub) ? (const void*)(static_cast<const char*>(d_sub) + (size_t)i * out_block)
                                           : nullptr;
+            fs.sq = (ps.final_ && d_sub && d_sq) ? d_sq + (size_t)i * residual_partials_per_slot(P) : nullptr;
             if (global) global_row_map(N, k, fs);
             ++i;
         }
@@ -560,6 +579,27 @@ drt3d_status drt3d_planes_forward_residual(const drt3d_plan* P, const void* d_in
                                            uint32_t mask, void* d_ws, size_t ws_bytes, cudaStream_t stream) {
     if (!d_target) return DRT3D_ERR_INVALID_ARG;
     return planes_forward_impl(P, d_in, d_out, mask, d_ws, ws_bytes, stream, false, d_target);
+}
+
+drt3d_status drt3d_planes_forward_residual_loss(const drt3d_plan* P, const void* d_in, const void* d_target,
+                                                void* d_out, uint32_t mask, double* d_loss, void* d_ws,
+                                                size_t ws_bytes, cudaStream_t stream) {
+    if (!P || !d_target || !d_loss) return DRT3D_ERR_INVALID_ARG;
+    if (P->dtype != DRT3D_F32) return DRT3D_ERR_DTYPE;
+    if (reinterpret_cast<uintptr_t>(d_loss) & 7) return DRT3D_ERR_ALIGN;
+    if (mask == 0 || (mask & ~DRT3D_ALL_DODECANTS)) return DRT3D_ERR_INVALID_ARG;
+    const size_t fwd = align_up((size_t)kMaxSlots * 2 * P->fused.buf_bytes, 256);
+    const long long per = residual_partials_per_slot(P);
+    if (!d_ws || ws_bytes < fwd + (size_t)kMaxSlots * per * sizeof(double)) return DRT3D_ERR_WORKSPACE;
+    if (!aligned16(d_ws)) return DRT3D_ERR_ALIGN;
+    double* part = reinterpret_cast<double*>(static_cast<char*>(d_ws) + fwd);
+    const drt3d_status st = planes_forward_impl(P, d_in, d_out, mask, d_ws, fwd, stream, false, d_target, part);
+    if (st != DRT3D_OK) return st;
+    prof_begin(P, stream, "planes_residual_loss", (double)popcount12(mask) * per * sizeof(double));
+    if (launch_residual_loss(part, (long long)popcount12(mask) * per, d_loss, stream) != cudaSuccess)
+        return DRT3D_ERR_CUDA;
+    prof_end(P, stream);
+    return DRT3D_OK;
 }
 
 drt3d_status drt3d_planes_forward_global(const drt3d_plan* P, const void* d_in, void* d_out, void* d_ws,

@@ -251,14 +251,18 @@ __device__ __forceinline__ void unpack_class_u16(int rr, const Chunks16 (&w)[1 <
 // values are either all valid or all past the tile: lanes past it return at
 // once, the others store one aligned vector per row (element stores only when
 // the output pitch rules vectors out).
-template <typename TOut, typename T, int G>
-__device__ __forceinline__ void store_rows(const FusedLaunch& L, const FusedSlot& sp, const T (&v)[1 << G][K],
-                                           int t1, int sg1, int wq1, int sg2, int wq2, int rs1, int rs2,
-                                           int d0, int lane) {
+// With SQ (float32 residual stores), returns the sum of the squares of the
+// residual cells this lane stored, else 0.
+template <typename TOut, typename T, int G, bool SQ = false>
+__device__ __forceinline__ float store_rows(const FusedLaunch& L, const FusedSlot& sp, const T (&v)[1 << G][K],
+                                            int t1, int sg1, int wq1, int sg2, int wq2, int rs1, int rs2,
+                                            int d0, int lane) {
     constexpr int R = 1 << G;
+    constexpr bool FSQ = SQ && std::is_same<TOut, float>::value;
     const int p0 = lane * K;
     const int d = d0 + p0;
-    if (p0 >= L.V || d >= L.dmax) return;
+    float sq = 0.f;
+    if (p0 >= L.V || d >= L.dmax) return sq;
     const int m0 = L.m0;
     const int o1 = t1 + (sg1 << G) + (wq1 << (m0 + G));
     const long long orow0 = (long long)o1 * rs1 + (long long)((sg2 << G) + (wq2 << (m0 + G))) * rs2;
@@ -287,7 +291,7 @@ __device__ __forceinline__ void store_rows(const FusedLaunch& L, const FusedSlot
                     st_global(dst + 3, e[3]);
                 }
             }
-            return;
+            return sq;
         }
     }
     TOut* out = static_cast<TOut*>(sp.out) + (d - L.gout.base);
@@ -311,13 +315,16 @@ __device__ __forceinline__ void store_rows(const FusedLaunch& L, const FusedSlot
                     TOut e[K], b[K];
                     memcpy(b, &bw[j], 16);
 #pragma unroll
-                    for (int i = 0; i < K; ++i) e[i] = (TOut)v[t0 + j][i] - b[i];
+                    for (int i = 0; i < K; ++i) {
+                        e[i] = (TOut)v[t0 + j][i] - b[i];
+                        if constexpr (FSQ) sq += e[i] * e[i];
+                    }
                     uint4 w;
                     memcpy(&w, e, 16);
                     st_global(reinterpret_cast<uint4*>(dst + (long long)(t0 + j) * rstride), w);
                 }
             }
-            return;
+            return sq;
         }
     }
     if (L.vec_store) {
@@ -343,9 +350,32 @@ __device__ __forceinline__ void store_rows(const FusedLaunch& L, const FusedSlot
             for (int i = 0; i < K; ++i)
                 if (d + i < L.dmax) {
                     TOut e = (TOut)v[t2][i];
-                    if (sub) e = e - sub[(long long)t2 * rstride + i];
+                    if (sub) {
+                        e = e - sub[(long long)t2 * rstride + i];
+                        if constexpr (FSQ) sq += e * e;
+                    }
                     st_global(dst + i, e);
                 }
+    }
+    return sq;
+}
+
+// The CTA's sum of its threads' squared residuals, written by thread 0: a
+// butterfly within each warp, then the warps in order (the same sum on every
+// run).  Every thread of the block must call it.
+template <int NW>
+__device__ __forceinline__ void write_cta_sq(double* dst, float s) {
+    __shared__ double red[NW];
+    double t = s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) a += red[w];
+        *dst = a;
     }
 }
 
@@ -355,9 +385,11 @@ __device__ __forceinline__ void store_rows(const FusedLaunch& L, const FusedSlot
 // read-only path (the batched kernel reads buffers other CTAs of the same
 // launch wrote).  PF compiles the launch-order L2 prefetch in (it reads
 // L.slot at a run-time index; a caller that keeps L in registers leaves it
-// out).
+// out).  SQ (float32 final passes with a residual target) writes the CTA's
+// sum of squared residual cells to sp.sq[cta]; then every warp of the block
+// must be one of the 2^G / GPW working warps.
 template <typename TIn, typename TOut, typename T, typename TS, int G, bool INGEST, bool COHERENT, bool TMA = false,
-          bool PF = true>
+          bool PF = true, bool SQ = false>
 __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot& sp, unsigned cta,
                                           unsigned char* smem_raw, const CUtensorMap* tmap = nullptr,
                                           int slot_z = 0, uint64_t* mbar = nullptr) {
@@ -408,6 +440,7 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
 
     if (zero_tile) {
         if (!active) return;
+        float sq = 0.f;
 #pragma unroll 1
         for (int gi = 0; gi < GPW; ++gi) {
             const int t1 = warp + gi * NW;
@@ -416,8 +449,9 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
             for (int r = 0; r < R; ++r)
 #pragma unroll
                 for (int i = 0; i < K; ++i) v[r][i] = T(0);
-            store_rows<TOut, T, G>(L, sp, v, t1, sg1, wq1, sg2, wq2, rs1, rs2, d0, lane);
+            sq += store_rows<TOut, T, G, SQ>(L, sp, v, t1, sg1, wq1, sg2, wq2, rs1, rs2, d0, lane);
         }
+        if constexpr (SQ) write_cta_sq<NW>(sp.sq + cta, sq);
         return;
     }
 
@@ -675,6 +709,7 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
     }
 
     // ---------------- phase 2: transform along axis 2, warp = t1 ----------
+    float sq = 0.f;
 #pragma unroll 1
     for (int gi = 0; gi < (active ? GPW : 0); ++gi) {
         const int t1 = warp + gi * NW;
@@ -695,8 +730,9 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
             for (int i = 0; i < K; ++i) v[u2][i] = (T)e[i];
         }
         fwd_all<G, K>(v);
-        store_rows<TOut, T, G>(L, sp, v, t1, sg1, wq1, sg2, wq2, rs1, rs2, d0, lane);
+        sq += store_rows<TOut, T, G, SQ>(L, sp, v, t1, sg1, wq1, sg2, wq2, rs1, rs2, d0, lane);
     }
+    if constexpr (SQ) write_cta_sq<NW>(sp.sq + cta, sq);
 }
 
 // ---------------------------------------------------------------------------

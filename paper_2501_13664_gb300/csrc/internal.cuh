@@ -141,6 +141,9 @@ struct FusedSlot {
     // Final pass only: when set, each output cell is stored minus the cell at
     // the same offset of this array (the residual of a least-squares fit).
     const void* sub;
+    // Final pass with `sub`, float32 only: when set, CTA c writes the sum of
+    // the squares of the residual cells it stored to sq[c].
+    double* sq;
 };
 
 struct FusedLaunch {
@@ -297,6 +300,8 @@ cudaError_t launch_planes_fused(const FusedLaunch& L, int G, ElemKind in_kind, E
 // input at G >= 3, 32-bit at G = 3), and that launch: `in_base` is slot 0's
 // input buffer, the other slots follow at `slot_stride` bytes.
 bool fused_uses_tma(int G, ElemKind in_kind, bool ingest);
+// loss[0] = 0.5 * sum of the n per-warp partial sums `part` (fixed order).
+cudaError_t launch_residual_loss(const double* part, long long n, double* loss, cudaStream_t s);
 cudaError_t launch_planes_fused_tma(const FusedLaunch& L, int G, ElemKind in_kind, ElemKind out_kind,
                                     const void* in_base, size_t slot_stride, int nslots, cudaStream_t s);
 // The tensor map of those staged loads (x = displacement - base, y = row,

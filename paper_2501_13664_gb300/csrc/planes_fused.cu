@@ -29,7 +29,9 @@ namespace {
 
 using namespace fused;
 
-template <typename TIn, typename TOut, typename T, typename TS, int G, bool INGEST>
+// SQ: float32 final pass that also sums the squared residual (one partial
+// per CTA, see fused_cta).
+template <typename TIn, typename TOut, typename T, typename TS, int G, bool INGEST, bool SQ = false>
 __global__ void __launch_bounds__(32 * fused_warps<G>(), (G >= 4 ? 2 : 1))
 planes_fused(const __grid_constant__ FusedLaunch L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -41,14 +43,14 @@ planes_fused(const __grid_constant__ FusedLaunch L) {
         else
             fused_cta<TIn, TOut, T, TS, G, INGEST, false>(L, L.slot[sl], blockIdx.x, smem_raw);
     } else {
-        fused_cta<TIn, TOut, T, TS, G, INGEST, false>(L, L.slot[sl], blockIdx.x, smem_raw);
+        fused_cta<TIn, TOut, T, TS, G, INGEST, false, false, true, SQ>(L, L.slot[sl], blockIdx.x, smem_raw);
     }
 }
 
-template <typename TIn, typename TOut, typename T, typename TS, int G, bool INGEST>
+template <typename TIn, typename TOut, typename T, typename TS, int G, bool INGEST, bool SQ = false>
 cudaError_t launch_g(const FusedLaunch& Lin, int nslots, cudaStream_t s) {
     const size_t smem = ((size_t)(1 << (2 * G)) * fused_ws<G>() + fused_pad<G>()) * sizeof(TS);
-    auto kern = planes_fused<TIn, TOut, T, TS, G, INGEST>;
+    auto kern = planes_fused<TIn, TOut, T, TS, G, INGEST, SQ>;
     static DeviceOnce attr_done;           // per instantiation
     static std::atomic<int> wave[64] = {};  // resident CTAs of the device, written before the flag
     int dev = 0;
@@ -77,7 +79,7 @@ cudaError_t launch_g(const FusedLaunch& Lin, int nslots, cudaStream_t s) {
 // staged by TMA: one 1-row box per (u2, u1) row window, landing in the
 // group's block of phase-1 results; one mbarrier per group counts the bytes.
 // T is the arithmetic type (uint32 ring or float), TIn the stored one.
-template <typename TIn, typename T, typename TOut, int G>
+template <typename TIn, typename T, typename TOut, int G, bool SQ = false>
 __global__ void __launch_bounds__(32 * fused_warps<G>(), (G >= 4 ? 2 : 1))
 planes_fused_tma(const __grid_constant__ FusedLaunch L, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -86,13 +88,13 @@ planes_fused_tma(const __grid_constant__ FusedLaunch L, const __grid_constant__ 
     // TMA destinations are kept 128-byte aligned.
     unsigned char* sm = smem_raw + ((128u - (tma::smem_u32(smem_raw) & 127u)) & 127u);
     const int sl = launch_slot(L.reverse_slots, blockIdx.y, gridDim.y);
-    fused_cta<TIn, TOut, T, T, G, false, false, true>(L, L.slot[sl], blockIdx.x, sm, &tmap, sl, mbar);
+    fused_cta<TIn, TOut, T, T, G, false, false, true, true, SQ>(L, L.slot[sl], blockIdx.x, sm, &tmap, sl, mbar);
 }
 
-template <typename TIn, typename T, typename TOut, int G>
+template <typename TIn, typename T, typename TOut, int G, bool SQ = false>
 cudaError_t launch_tma_g(const FusedLaunch& L, const CUtensorMap& map, int nslots, cudaStream_t s) {
     const size_t smem = ((size_t)(1 << G) * group_elems<TIn, G, true>() + fused_pad<G>()) * 4 + 128;
-    auto kern = planes_fused_tma<TIn, T, TOut, G>;
+    auto kern = planes_fused_tma<TIn, T, TOut, G, SQ>;
     static DeviceOnce attr_done;  // per instantiation
     int dev = 0;
     cudaGetDevice(&dev);
@@ -129,6 +131,17 @@ template <typename TIn, typename TOut, typename T, bool INGEST>
 cudaError_t launch_fused_t(const FusedLaunch& L, int G, int nslots, cudaStream_t s) {
     constexpr bool narrow = INGEST && std::is_same<TIn, uint8_t>::value;
     using TS = typename std::conditional<narrow, uint16_t, T>::type;
+    if constexpr (std::is_same<TOut, float>::value) {
+        if (L.slot[0].sq) {  // final float32 pass summing the squared residual
+            switch (G) {
+            case 1: return launch_g<TIn, TOut, T, TS, 1, INGEST, true>(L, nslots, s);
+            case 2: return launch_g<TIn, TOut, T, TS, 2, INGEST, true>(L, nslots, s);
+            case 3: return launch_g<TIn, TOut, T, TS, 3, INGEST, true>(L, nslots, s);
+            case 4: return launch_g<TIn, TOut, T, TS, 4, INGEST, true>(L, nslots, s);
+            }
+            return cudaErrorInvalidValue;
+        }
+    }
     switch (G) {
     case 1: return launch_g<TIn, TOut, T, TS, 1, INGEST>(L, nslots, s);
     case 2: return launch_g<TIn, TOut, T, TS, 2, INGEST>(L, nslots, s);
@@ -138,7 +151,38 @@ cudaError_t launch_fused_t(const FusedLaunch& L, int G, int nslots, cudaStream_t
     return cudaErrorInvalidValue;
 }
 
+// loss[0] = 0.5 * sum of part[0 .. n): one block; thread t adds the entries
+// t + j 1024 into accumulator j mod 4 (four independent chains, loads in
+// flight together), then the four in order and a fixed tree over the threads
+// (the same sum on every run).
+constexpr int kLossThreads = 1024;
+__global__ void __launch_bounds__(kLossThreads) residual_loss_sum(const double* __restrict__ part, long long n,
+                                                                  double* __restrict__ loss) {
+    pdl_wait_and_release();
+    __shared__ double red[kLossThreads];
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long i = threadIdx.x; i < n; i += 4LL * kLossThreads) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long long k = i + (long long)j * kLossThreads;
+            if (k < n) a[j] += part[k];
+        }
+    }
+    red[threadIdx.x] = (a[0] + a[1]) + (a[2] + a[3]);
+    __syncthreads();
+#pragma unroll 1
+    for (int h = kLossThreads / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loss[0] = 0.5 * red[0];
+}
+
 }  // namespace
+
+cudaError_t launch_residual_loss(const double* part, long long n, double* loss, cudaStream_t s) {
+    return launch_chained(residual_loss_sum, dim3(1), dim3(kLossThreads), 0, s, part, n, loss);
+}
 
 int fused_lanes_k() { return K; }
 int fused_valid(int G) {
@@ -219,9 +263,11 @@ cudaError_t launch_planes_fused_tma(const FusedLaunch& L, int G, ElemKind in_kin
         return to16 ? launch_tma_g<uint16_t, uint32_t, uint16_t, 4>(L, map, nslots, s)
                     : launch_tma_g<uint16_t, uint32_t, uint32_t, 4>(L, map, nslots, s);
     }
-    if (in_kind == ElemKind::F32)
-        return out_kind == ElemKind::F32 ? launch_tma_g<float, float, float, 3>(L, map, nslots, s)
-                                         : cudaErrorInvalidValue;
+    if (in_kind == ElemKind::F32) {
+        if (out_kind != ElemKind::F32) return cudaErrorInvalidValue;
+        return L.slot[0].sq ? launch_tma_g<float, float, float, 3, true>(L, map, nslots, s)
+                            : launch_tma_g<float, float, float, 3>(L, map, nslots, s);
+    }
     return out_kind == ElemKind::I32 ? launch_tma_g<uint32_t, uint32_t, uint32_t, 3>(L, map, nslots, s)
                                      : cudaErrorInvalidValue;
 }

@@ -12,16 +12,17 @@ from __future__ import annotations
 
 import torch
 
-from . import ALL, _mask, get_plan, planes_adjoint, planes_forward, planes_forward_residual
+from . import ALL, _mask, get_plan, planes_adjoint, planes_forward, planes_forward_residual_loss
 
 
 class LeastSquaresLoss(torch.autograd.Function):
     """0.5 ||A x - b||^2 over a batch, with A the planes transform.
 
     Forward computes the residual r = A x - b in the transform's own store
-    (one pass over b, none over A x) and the loss from r; backward is the
-    hand-written adjoint (backprojection) of r, scaled by the incoming
-    gradient.  r is kept between the two (the one tensor of the size of b).
+    (one pass over b, none over A x) and the loss as r is stored (no pass
+    over r); backward is the hand-written adjoint (backprojection) of r,
+    scaled by the incoming gradient.  r is kept between the two (the one
+    tensor of the size of b).
     """
 
     @staticmethod
@@ -32,13 +33,13 @@ class LeastSquaresLoss(torch.autograd.Function):
         B, N = int(x.shape[0]), int(x.shape[1])
         m = _mask(dodecants)
         r = torch.empty_like(b)
-        ws = get_plan(N, torch.float32).workspace("planes_forward")
+        losses = torch.empty((B,), dtype=torch.float64, device=x.device)
+        ws = get_plan(N, torch.float32).workspace("planes_residual_loss")
         for i in range(B):
-            planes_forward_residual(x[i], b[i], m, out=r[i], workspace=ws)
+            planes_forward_residual_loss(x[i], b[i], m, out=r[i], loss=losses[i], workspace=ws)
         ctx.save_for_backward(r)
         ctx.mask = m
-        # one float32 pass over r (a float64 norm would first copy r to float64)
-        return 0.5 * torch.linalg.vector_norm(r).double() ** 2
+        return losses.sum()
 
     @staticmethod
     def backward(ctx, g: torch.Tensor):
@@ -53,8 +54,8 @@ class LeastSquaresLoss(torch.autograd.Function):
 
 
 def least_squares_loss(x: torch.Tensor, b: torch.Tensor, dodecants=ALL) -> torch.Tensor:
-    """0.5 ||A x - b||^2 (float64 scalar; the norm of the float32 residual is
-    accumulated in float32) for (B, N, N, N) float32 x and
+    """0.5 ||A x - b||^2 (float64 scalar; squares of the float32 residual
+    added per lane in float32, then in float64) for (B, N, N, N) float32 x and
     (B, k, N, N, 3N) float32 targets; differentiable in x."""
     return LeastSquaresLoss.apply(x, b, _mask(dodecants))
 

@@ -113,6 +113,24 @@ def test_forward_residual_is_forward_minus_target(drt, N, dt):
     assert torch.equal(b2, want)
 
 
+@pytest.mark.parametrize("N,mask", [(16, 0xFFF), (32, 0xFFF), (64, 0b100100010001)])
+def test_residual_loss_is_half_the_squared_residual(drt, N, mask):
+    """The loss summed in the last pass's stores equals 0.5 * sum r^2 of the
+    residual it stored (float64 over the float32 cells), is the same on every
+    call (fixed summation order), and leaves r bit for bit as the plain
+    residual entry writes it."""
+    ks = [k for k in range(12) if (mask >> k) & 1]
+    x = torch.from_numpy(synth.random_float((N, N, N), 41)).cuda()
+    b = torch.from_numpy(synth.random_float((len(ks), N, N, 3 * N), 42)).cuda()
+    r_ref = drt.planes_forward_residual(x, b, ks)
+    r, loss = drt.planes_forward_residual_loss(x, b, ks)
+    assert torch.equal(r, r_ref)
+    ref = 0.5 * float((r_ref.double() ** 2).sum())
+    assert abs(float(loss) - ref) <= 1e-6 * ref
+    _, loss2 = drt.planes_forward_residual_loss(x, b, ks)
+    assert float(loss2) == float(loss)
+
+
 def test_least_squares_loss_matches_autograd_of_mse(drt):
     """The least-squares autograd function (residual in the forward's store,
     adjoint of the saved residual) gives the same gradient, bit for bit, as
