@@ -497,14 +497,16 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
     if constexpr (TMA) {
         // Stage every group's rows: one 1-row box per (u2, u1); a group whose
         // windows all miss the stored range issues nothing (its warp parks
-        // zeros below, the same test decides both).
-        if (threadIdx.x == 0) {
-#pragma unroll 1
-            for (int g = 0; g < R; ++g) tma::mbar_init(&mbar[g], 1);
-            tma::fence_barrier_init();
-        }
-        __syncthreads();
+        // zeros below, the same test decides both).  A group's barrier is
+        // used by its own warp only (initialised, armed, waited on and
+        // retired there), so no block-wide barrier precedes the loads.
         if (active) {
+            if (lane == 0) {
+#pragma unroll 1
+                for (int gi = 0; gi < GPW; ++gi) tma::mbar_init(&mbar[warp + gi * NW], 1);
+                tma::fence_barrier_init();
+            }
+            __syncwarp();
 #pragma unroll 1
             for (int gi = 0; gi < GPW; ++gi) {
                 const int u2 = warp + gi * NW;
@@ -595,6 +597,9 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
                         for (int i = 0; i < K; ++i) dst[i] = TS(0);
                     }
                 }
+                if constexpr (TMA) {
+                    if (lane == 0) tma::mbar_inval(&mbar[u2]);  // never armed
+                }
                 continue;
             }
             const TIn* buf = static_cast<const TIn*>(sp.in);
@@ -603,9 +608,12 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
             if constexpr (TMA) {
                 // Wait for the group's staged rows, then read each lane's 4
                 // elements at the row's offset inside its 16-byte-aligned box.
-                if (!tma::mbar_wait(&mbar[u2], 0, kTmaWaitNs)) {
-                    if (lane == 0 && L.status) atomicCAS(L.status, 0, (int)DRT3D_ERR_TIMEOUT);
-                }
+                const bool landed = tma::mbar_wait(&mbar[u2], 0, kTmaWaitNs);
+                if (!landed && L.status) atomicCAS(L.status, 0, (int)DRT3D_ERR_TIMEOUT);
+                // Retire the group's barrier once every lane has seen it
+                // complete (after a time-out a load may still be pending:
+                // leave it).
+                if (__all_sync(0xffffffffu, landed) && lane == 0) tma::mbar_inval(&mbar[u2]);
                 const int a = sg1 & 3, c = g_lo & 3;
                 if constexpr (sizeof(TIn) == 2) {
                     // Two 8-byte reads per row from the 4-aligned element below
@@ -698,15 +706,6 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
         }
     }
     __syncthreads();
-    if constexpr (TMA) {
-        // Every armed barrier has completed (its warp waited above): retire
-        // them before this shared memory is used again.
-        // (After a recorded time-out a load may still be pending: leave them.)
-        if (threadIdx.x == 0 && !(L.status && *(volatile int*)L.status == (int)DRT3D_ERR_TIMEOUT)) {
-#pragma unroll 1
-            for (int g = 0; g < R; ++g) tma::mbar_inval(&mbar[g]);
-        }
-    }
 
     // ---------------- phase 2: transform along axis 2, warp = t1 ----------
     float sq = 0.f;
