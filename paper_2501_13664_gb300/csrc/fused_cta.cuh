@@ -201,28 +201,44 @@ __device__ __forceinline__ T from_bits(uint32_t x) {
     else return (T)x;
 }
 
-// Staged 32-bit rows of residue class J (u1 = J mod 4): the box starts at the
-// 4-aligned element below the window, so lane L's chunk is at 4L and its
-// elements are rr .. rr + 3 of the eight there (the second 16-byte read only
-// when rr > 0).
-template <int RR, typename T>
-__device__ __forceinline__ void take4_u32(const uint32_t* p, T (&v)[K]) {
-    const uint4 a = *reinterpret_cast<const uint4*>(p);
-    uint32_t x[8] = {a.x, a.y, a.z, a.w, 0u, 0u, 0u, 0u};
-    if constexpr (RR > 0) {
-        const uint4 b = *reinterpret_cast<const uint4*>(p + 4);
-        x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+// Words LO .. HI of a staged row from q, each read with the widest aligned
+// shared-memory access up to MAXV words (q is aligned to MAXV words): a lane
+// reads only the words its window needs, fewer wavefronts than whole 16-byte
+// chunks around it.
+template <int LO, int HI, int MAXV>
+__device__ __forceinline__ void lds_words(const uint32_t* q, uint32_t (&w)[8]) {
+    if constexpr (LO <= HI) {
+        if constexpr (MAXV >= 4 && LO % 4 == 0 && LO + 3 <= HI) {
+            const uint4 x = *reinterpret_cast<const uint4*>(q + LO);
+            w[LO] = x.x; w[LO + 1] = x.y; w[LO + 2] = x.z; w[LO + 3] = x.w;
+            lds_words<LO + 4, HI, MAXV>(q, w);
+        } else if constexpr (MAXV >= 2 && LO % 2 == 0 && LO + 1 <= HI) {
+            const uint2 x = *reinterpret_cast<const uint2*>(q + LO);
+            w[LO] = x.x; w[LO + 1] = x.y;
+            lds_words<LO + 2, HI, MAXV>(q, w);
+        } else {
+            w[LO] = q[LO];
+            lds_words<LO + 1, HI, MAXV>(q, w);
+        }
     }
-#pragma unroll
-    for (int i = 0; i < K; ++i) v[i] = from_bits<T>(x[RR + i]);
 }
 
+// Staged 32-bit rows of residue class J (u1 = J mod 4): the box starts at the
+// 4-aligned element below the window, so lane L's chunk is at 4L and its
+// elements are rr .. rr + 3 (and, for the odd rows, rr + 4, which stage 0
+// takes instead of a shuffle) of the eight there.
 template <int J, int G, typename T>
-__device__ __forceinline__ void stage_class_u32(int rr, const uint32_t* st, int lane, T (&v)[1 << G][K]) {
+__device__ __forceinline__ void stage_class_u32(int rr, const uint32_t* st, int lane, T (&v)[1 << G][K],
+                                                T (&nxt)[1 << (G - 1)]) {
     constexpr int RW = Stage<uint32_t>::ROW_BYTES / 4;  // words between staged rows
-#define DRT3D_STAGE_CLASS(RRV)                                  \
-    _Pragma("unroll") for (int u1 = J; u1 < (1 << G); u1 += 4) \
-        take4_u32<RRV, T>(st + u1 * RW + lane * K, v[u1]);
+    constexpr int NE = (J & 1) ? K + 1 : K;
+#define DRT3D_STAGE_CLASS(RRV)                                                             \
+    _Pragma("unroll") for (int u1 = J; u1 < (1 << G); u1 += 4) {                           \
+        uint32_t w[8];                                                                     \
+        lds_words<(RRV), (RRV) + NE - 1, 4>(st + u1 * RW + lane * K, w);                   \
+        _Pragma("unroll") for (int i = 0; i < K; ++i) v[u1][i] = from_bits<T>(w[(RRV) + i]); \
+        if constexpr ((J & 1) != 0) nxt[u1 >> 1] = from_bits<T>(w[(RRV) + K]);            \
+    }
     switch (rr) {
     case 0: DRT3D_STAGE_CLASS(0) break;
     case 1: DRT3D_STAGE_CLASS(1) break;
@@ -230,6 +246,36 @@ __device__ __forceinline__ void stage_class_u32(int rr, const uint32_t* st, int 
     default: DRT3D_STAGE_CLASS(3) break;
     }
 #undef DRT3D_STAGE_CLASS
+}
+
+__device__ __forceinline__ uint32_t u16_at(const uint32_t (&w)[8], int e) {
+    return (e & 1) ? (w[e >> 1] >> 16) : (w[e >> 1] & 0xFFFFu);
+}
+
+// Staged 16-bit rows of residue class J (u1 = J mod 4) at window offset rr:
+// each row's K elements, and for the odd rows also the element after them
+// (stage 0 adds it instead of shuffling it from the next lane).
+template <int J, int G, typename T>
+__device__ __forceinline__ void stage_class_u16(int rr, const uint16_t* st, int g_lo, int sg1, int lane,
+                                                T (&v)[1 << G][K], T (&nxt)[1 << (G - 1)]) {
+    constexpr int RW = Stage<uint16_t>::ROW_BYTES / 2;  // elements between staged rows
+    constexpr int NE = (J & 1) ? K + 1 : K;
+#define DRT3D_STAGE_U16(RRV)                                                             \
+    _Pragma("unroll") for (int u1 = J; u1 < (1 << G); u1 += 4) {                         \
+        uint32_t w[8];                                                                   \
+        lds_words<(RRV) / 2, ((RRV) + NE - 1) / 2, 2>(                                   \
+            reinterpret_cast<const uint32_t*>(st + u1 * RW + ((g_lo + sg1 * u1) & 4) + lane * K), w); \
+        _Pragma("unroll") for (int i = 0; i < K; ++i)                                    \
+            v[u1][i] = to_acc<uint16_t, T>((uint16_t)u16_at(w, RRV + i));                \
+        if constexpr ((J & 1) != 0) nxt[u1 >> 1] = to_acc<uint16_t, T>((uint16_t)u16_at(w, RRV + K)); \
+    }
+    switch (rr) {
+    case 0: DRT3D_STAGE_U16(0) break;
+    case 1: DRT3D_STAGE_U16(1) break;
+    case 2: DRT3D_STAGE_U16(2) break;
+    default: DRT3D_STAGE_U16(3) break;
+    }
+#undef DRT3D_STAGE_U16
 }
 
 template <int J, int G, typename T>
@@ -620,30 +666,29 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
                     // the window; the in-chunk offset repeats with u1 mod 4 (as
                     // for the register path) and is unpacked at a compile-time
                     // offset.
+                    // Each row's words are read at a compile-time offset per
+                    // class; the odd rows also supply the element past the
+                    // lane's window, which stage 0 takes instead of a shuffle.
                     const uint16_t* st = reinterpret_cast<const uint16_t*>(smem_raw + (size_t)u2 * GB * sizeof(TS));
-                    Chunks16 w[R];
-#pragma unroll
-                    for (int u1 = 0; u1 < R; ++u1) {
-                        const uint16_t* src =
-                            st + u1 * (Stage<TIn>::ROW_BYTES / 2) + ((g_lo + sg1 * u1) & 4) + lane * K;
-                        w[u1].c[0] = *reinterpret_cast<const uint2*>(src);
-                        w[u1].c[1] = *reinterpret_cast<const uint2*>(src + 4);
-                    }
+                    T nxt[R / 2];
+                    stage_class_u16<0, G>(c, st, g_lo, sg1, lane, v, nxt);
+                    stage_class_u16<1, G>((c + a) & 3, st, g_lo, sg1, lane, v, nxt);
+                    stage_class_u16<2, G>((c + 2 * a) & 3, st, g_lo, sg1, lane, v, nxt);
+                    stage_class_u16<3, G>((c + 3 * a) & 3, st, g_lo, sg1, lane, v, nxt);
                     __syncwarp();  // the group's results overwrite its staging
-                    unpack_class_u16<0, G>(c, w, v);
-                    if constexpr (R > 1) unpack_class_u16<1, G>((c + a) & 3, w, v);
-                    if constexpr (R > 2) unpack_class_u16<2, G>((c + 2 * a) & 3, w, v);
-                    if constexpr (R > 3) unpack_class_u16<3, G>((c + 3 * a) & 3, w, v);
+                    fwd_stage0_nxt<G, K>(v, nxt);
                 } else {
                     // 32-bit rows: one or two 16-byte reads per row at the
                     // lane's chunk, taken by residue class at a compile-time
                     // offset.
                     const uint32_t* st = reinterpret_cast<const uint32_t*>(smem_raw + (size_t)u2 * GB * sizeof(TS));
-                    stage_class_u32<0, G>(c, st, lane, v);
-                    if constexpr (R > 1) stage_class_u32<1, G>((c + a) & 3, st, lane, v);
-                    if constexpr (R > 2) stage_class_u32<2, G>((c + 2 * a) & 3, st, lane, v);
-                    if constexpr (R > 3) stage_class_u32<3, G>((c + 3 * a) & 3, st, lane, v);
+                    T nxt[R / 2];
+                    stage_class_u32<0, G>(c, st, lane, v, nxt);
+                    stage_class_u32<1, G>((c + a) & 3, st, lane, v, nxt);
+                    stage_class_u32<2, G>((c + 2 * a) & 3, st, lane, v, nxt);
+                    stage_class_u32<3, G>((c + 3 * a) & 3, st, lane, v, nxt);
                     __syncwarp();  // the group's results overwrite its staging
+                    fwd_stage0_nxt<G, K>(v, nxt);
                 }
             } else if constexpr (sizeof(TIn) == 2) {
                 const int L0 = start - L.gin.base;  // window offset of row u1 = 0
@@ -685,7 +730,8 @@ __device__ __forceinline__ void fused_cta(const FusedLaunch& L, const FusedSlot&
                 }
             }
         }
-        fwd_all<G, K>(v);
+        if constexpr (TMA) fwd_all<G, K, 1>(v);  // stage 0 done with the staged reads
+        else fwd_all<G, K>(v);
         if (lane * K < WS) {
 #pragma unroll
             for (int t1 = 0; t1 < R; ++t1) {

@@ -72,6 +72,30 @@ __device__ __forceinline__ void fwd_stage(T (&v)[1 << G][K]) {
         for (int i = 0; i < K; ++i) v[r][i] = nv[r][i];
 }
 
+// Stage 0 with the value one position past the lane's last of each odd row
+// supplied by the caller (nxt[q] for row 2q + 1, read along with the row)
+// instead of taken from the next lane by a shuffle.
+template <int G, int K, typename T>
+__device__ __forceinline__ void fwd_stage0_nxt(T (&v)[1 << G][K], const T (&nxt)[1 << (G - 1)]) {
+    constexpr int R = 1 << G;
+    T nv[R][K];
+#pragma unroll
+    for (int q = 0; q < R / 2; ++q) {
+        T ext[K + 1];
+#pragma unroll
+        for (int i = 0; i < K; ++i) ext[i] = v[2 * q + 1][i];
+        ext[K] = nxt[q];
+#pragma unroll
+        for (int lsb = 0; lsb < 2; ++lsb)
+#pragma unroll
+            for (int i = 0; i < K; ++i) nv[2 * q + lsb][i] = v[2 * q][i] + ext[i + lsb];
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int i = 0; i < K; ++i) v[r][i] = nv[r][i];
+}
+
 template <int G, int K, int J = 0, bool ZB = false, typename T>
 __device__ __forceinline__ void fwd_all(T (&v)[1 << G][K]) {
     if constexpr (J < G) {
