@@ -202,9 +202,7 @@ __device__ __forceinline__ T from_bits(uint32_t x) {
 }
 
 // Words LO .. HI of a staged row from q, each read with the widest aligned
-// shared-memory access up to MAXV words (q is aligned to MAXV words): a lane
-// reads only the words its window needs, fewer wavefronts than whole 16-byte
-// chunks around it.
+// shared-memory access up to MAXV words (q is aligned to MAXV words).
 template <int LO, int HI, int MAXV>
 __device__ __forceinline__ void lds_words(const uint32_t* q, uint32_t (&w)[8]) {
     if constexpr (LO <= HI) {
@@ -225,19 +223,26 @@ __device__ __forceinline__ void lds_words(const uint32_t* q, uint32_t (&w)[8]) {
 
 // Staged 32-bit rows of residue class J (u1 = J mod 4): the box starts at the
 // 4-aligned element below the window, so lane L's chunk is at 4L and its
-// elements are rr .. rr + 3 (and, for the odd rows, rr + 4, which stage 0
-// takes instead of a shuffle) of the eight there.
+// elements are rr .. rr + 3 of the eight there, read as whole 16-byte chunks
+// (lanes 16 bytes apart: a narrower read would conflict on the banks and cost
+// as many wavefronts); the second chunk only when rr > 0.  The odd rows also
+// give stage 0 the element after the window: element rr + 4 of the chunks
+// when rr > 0, else the next lane's first element, shuffled (rr is the same
+// for the whole warp).
 template <int J, int G, typename T>
 __device__ __forceinline__ void stage_class_u32(int rr, const uint32_t* st, int lane, T (&v)[1 << G][K],
                                                 T (&nxt)[1 << (G - 1)]) {
     constexpr int RW = Stage<uint32_t>::ROW_BYTES / 4;  // words between staged rows
-    constexpr int NE = (J & 1) ? K + 1 : K;
-#define DRT3D_STAGE_CLASS(RRV)                                                             \
-    _Pragma("unroll") for (int u1 = J; u1 < (1 << G); u1 += 4) {                           \
-        uint32_t w[8];                                                                     \
-        lds_words<(RRV), (RRV) + NE - 1, 4>(st + u1 * RW + lane * K, w);                   \
-        _Pragma("unroll") for (int i = 0; i < K; ++i) v[u1][i] = from_bits<T>(w[(RRV) + i]); \
-        if constexpr ((J & 1) != 0) nxt[u1 >> 1] = from_bits<T>(w[(RRV) + K]);            \
+    constexpr bool ODD = (J & 1) != 0;
+#define DRT3D_STAGE_CLASS(RRV)                                                                 \
+    _Pragma("unroll") for (int u1 = J; u1 < (1 << G); u1 += 4) {                               \
+        uint32_t w[8];                                                                         \
+        lds_words<0, ((RRV) > 0 ? 7 : 3), 4>(st + u1 * RW + lane * K, w);                        \
+        _Pragma("unroll") for (int i = 0; i < K; ++i) v[u1][i] = from_bits<T>(w[(RRV) + i]);  \
+        if constexpr (ODD) {                                                                   \
+            if constexpr ((RRV) > 0) nxt[u1 >> 1] = from_bits<T>(w[(RRV) + K]);               \
+            else nxt[u1 >> 1] = shfl_down(v[u1][0], 1);                                        \
+        }                                                                                      \
     }
     switch (rr) {
     case 0: DRT3D_STAGE_CLASS(0) break;
@@ -254,7 +259,10 @@ __device__ __forceinline__ uint32_t u16_at(const uint32_t (&w)[8], int e) {
 
 // Staged 16-bit rows of residue class J (u1 = J mod 4) at window offset rr:
 // each row's K elements, and for the odd rows also the element after them
-// (stage 0 adds it instead of shuffling it from the next lane).
+// (stage 0 adds it instead of shuffling it from the next lane).  Lanes are
+// 8 bytes apart, so a 4- or 8-byte read costs two wavefronts: the words the
+// window needs take two (rr = 0, four elements) or four, never more than the
+// two 8-byte reads of the whole chunk pair.
 template <int J, int G, typename T>
 __device__ __forceinline__ void stage_class_u16(int rr, const uint16_t* st, int g_lo, int sg1, int lane,
                                                 T (&v)[1 << G][K], T (&nxt)[1 << (G - 1)]) {

@@ -78,9 +78,12 @@ cudaError_t launch_g(const FusedLaunch& Lin, int nslots, cudaStream_t s) {
 // Pass over buffer rows (16-bit, or 32-bit at G = 3) with the phase-1 input
 // staged by TMA: one 1-row box per (u2, u1) row window, landing in the
 // group's block of phase-1 results; one mbarrier per group counts the bytes.
-// T is the arithmetic type (uint32 ring or float), TIn the stored one.
+// T is the arithmetic type (uint32 ring or float), TIn the stored one.  At
+// G = 3 four CTAs share an SM (64 registers: the 32-bit variants spill a few
+// words, and still beat three CTAs at 80 registers, 1.21 -> 1.17 ms for the
+// final float32 pass of 8 volumes of 128^3).
 template <typename TIn, typename T, typename TOut, int G, bool SQ = false>
-__global__ void __launch_bounds__(32 * fused_warps<G>(), (G >= 4 ? 2 : 1))
+__global__ void __launch_bounds__(32 * fused_warps<G>(), (G >= 4 ? 2 : 4))
 planes_fused_tma(const __grid_constant__ FusedLaunch L, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar[1 << G];
