@@ -42,6 +42,19 @@ def test_forward_integer_exact(drt, oracle_mod, N, dt):
     np.testing.assert_array_equal(_fwd(drt, f), oracle_mod.planes_forward(f))
 
 
+@pytest.mark.parametrize("N", [64, 128])
+@pytest.mark.parametrize("dt", ["i16", "i32"])
+def test_forward_wide_dtypes_mid_sizes_exact(drt, oracle_mod, N, dt):
+    """int16 and full-range int32 volumes at the sizes whose final pass reads
+    32-bit rows staged by TMA (G = 3 under the default splits (3, 3) at N = 64
+    and (4, 3) at N = 128): every cell against the oracle."""
+    if dt == "i16":
+        f = synth.random_int32((N, N, N), 40 + N, -32768, 32768).astype(np.int16)
+    else:
+        f = synth.random_int32((N, N, N), 41 + N)
+    np.testing.assert_array_equal(_fwd(drt, f), oracle_mod.planes_forward(f))
+
+
 @pytest.mark.parametrize("mask", [0x001, 0x800, 0x0A5, 0xF0F])
 def test_forward_dodecant_subsets(drt, oracle_mod, mask):
     N = 16
@@ -156,7 +169,7 @@ def test_embedded_planes_over_dense_background(drt, oracle_mod, N):
         assert int(R[k, s1, s2, dp + 2 * N]) == want, (k, s1, s2, dp)
 
 
-@pytest.mark.parametrize("N", [4, 16, 64])
+@pytest.mark.parametrize("N", [4, 16, 64, 128])
 def test_forward_float_within_tolerance(drt, oracle_mod, N):
     x = synth.random_float((N, N, N), 7)
     got = _fwd(drt, x).astype(np.float64)
