@@ -74,8 +74,6 @@ struct Stage {
     static constexpr int ELEMS = WT + 16 / (int)sizeof(TIn);
     static constexpr int ROW_BYTES = (ELEMS * (int)sizeof(TIn) + 127) / 128 * 128;
 };
-constexpr int kStageElems = Stage<uint16_t>::ELEMS;
-constexpr int kStageRowBytes = Stage<uint16_t>::ROW_BYTES;
 
 // Elements (of the 32-bit phase-1 result type when staged) of one group's
 // block of shared memory: its 2^G result rows of WS, or its staging if that is
